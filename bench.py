@@ -1,0 +1,374 @@
+"""Benchmark: GCUPS of the Smith-Waterman database search on GB300.
+
+One step = one pass of the whole search (query profiles, inter-task int16x2 kernel,
+intra-task kernel for long subjects, int32 rescore of saturated lanes) for a batch of
+queries against the device-resident database.  Default workload: the 20 paper-shaped query
+lengths (144..5478, sum 30,747) against a seeded synthetic database of 1M protein
+sequences (log-normal lengths, mean 250, clipped to 20..2000; ~249M residues), BLOSUM62,
+a gap of length k costing 10 + 2(k - 1).  GCUPS = sum(|Q|) * |D| / (t * 1e9) (paper
+Eq. gcups).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank searches its own database of the
+same size (weak scaling; no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+# Issue-rate roofline of the inter-task kernel (derivation in the design doc): 128 int16x2 DPX
+# lane-operations per clock per SM (measured), two cells per lane-operation, and 6.5 issued
+# operations per cell pair (5 DPX updates + 0.5 three-way max + 1 byte permute).
+LANE_OPS_PER_CLK_SM = 128
+OPS_PER_CELL_PAIR = 6.5
+INTER_KERNEL = "k_inter_i16x2"
+INTER_SRC = os.path.join(ROOT, "paper_1702_07195_gb300", "csrc", "k_inter.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "plain", "paper_shaped", "long_subject"])
+    ap.add_argument("--scale", type=float, default=1.0, help="database scale (tests only)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+WORKLOAD_TEXT = {
+    "batched": "20 queries (lengths 144..5478 log-uniform, sum 30,747) vs 1M synthetic protein "
+               "sequences (log-normal lengths mean 250, clip 20..2000), BLOSUM62, gaps 10/2",
+    "plain": "1 query of 144 vs 10,000 synthetic protein sequences (log-normal mean 250, clip "
+             "20..2000), BLOSUM62, gaps 10/2",
+    "paper_shaped": "20 queries (144..5478) vs 6M synthetic sequences (log-normal mean 250, "
+                    "sigma 1.0, clip 20..35,000), BLOSUM62, gaps 10/2",
+    "long_subject": "5 queries (1,000..5,000) vs 50,000 synthetic sequences uniform over "
+                    "5,000..35,000, BLOSUM62, gaps 10/2",
+}
+
+
+def make_workload(name, seed, scale):
+    return getattr(w, name)(seed=seed, scale=scale)
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the inter-task kernel from the committed ncu summary, or None
+    if the summary is absent or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{INTER_KERNEL}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    src = hashlib.sha256(open(INTER_SRC, "rb").read()).hexdigest()[:16]
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_src or not m_b or m_src.group(1) != src:
+        return None
+    return float(m_b.group(1))
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------- oracle baseline
+def cpu_baseline(wl, seconds, seed):
+    """The oracle (as it stands) on the host cores, on a seeded sample of the database sized
+    for about `seconds` of CPU work.  Returns the cpu_baseline dict."""
+    import oracle
+    oracle.build()
+    total_m = sum(len(q) for q in wl.queries)
+    n = wl.db.num_seqs
+    # calibrate on a small sample
+    probe = w.sample_indices(n, min(n, 200), seed=seed + 1)
+    sub = wl.db.subset(probe)
+    t0 = time.perf_counter()
+    _, cores = oracle.sw_search(wl.queries[0], sub.residues, sub.offsets, wl.matrix,
+                                wl.gap_open, wl.gap_extend)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    rate = len(wl.queries[0]) * sub.num_residues / dt
+    want_res = max(1, int(rate * seconds / total_m))
+    mean_len = max(1.0, wl.db.num_residues / max(1, n))
+    count = int(min(n, max(16, want_res / mean_len)))
+    idx = w.sample_indices(n, count, seed=seed + 2)
+    sub = wl.db.subset(idx)
+    t0 = time.perf_counter()
+    for q in wl.queries:
+        oracle.sw_search(q, sub.residues, sub.offsets, wl.matrix, wl.gap_open, wl.gap_extend)
+    dt = time.perf_counter() - t0
+    cells = total_m * sub.num_residues
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": int(cores), "kind": "oracle",
+            "sample": f"all {len(wl.queries)} queries vs a seeded sample of {count} of the "
+                      f"{n} database sequences ({sub.num_residues} residues, {cells:.3e} cells,"
+                      f" {dt:.1f} s)",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, args.seed, args.scale)
+    vals = []
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, per_step, args.seed + 17 * i)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    value = statistics.mean(vals) if vals else cb["value"]
+    cb["value"] = value
+    line = {"impl": "reference", "metric": "GCUPS", "value": value, "unit": "GCUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * cb["seconds"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload],
+                       "queries": len(wl.queries), "db_seqs": wl.db.num_seqs,
+                       "db_residues": wl.db.num_residues},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- our path
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1702_07195_gb300 as sw
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = make_workload(args.workload, args.seed + rank, args.scale)
+    nq = len(wl.queries)
+    cat = np.concatenate(wl.queries)
+    qoff = np.zeros(nq + 1, np.int64)
+    np.cumsum([len(q) for q in wl.queries], out=qoff[1:])
+    db = sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE)
+    N = db.num_seqs
+    d_q = torch.from_numpy(cat).cuda()
+    d_s = torch.empty(nq * N, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    cells = int(cat.size) * wl.db.num_residues
+
+    def step():
+        sw.sw_search_batch_device(db, d_q, qoff, wl.matrix, wl.gap_open, wl.gap_extend, d_s,
+                                  stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = sw.sw_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    inter_ms, flagged = [], 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        st = sw.sw_get_stats(db)          # per-kernel CUDA events on the launch stream
+        inter_ms.append(st["inter_ms"])
+        flagged += st["flagged"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sw.sw_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * cells / (t_max * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_q = [torch.from_numpy(q).pin_memory() for q in wl.queries]
+        h_s = torch.empty(nq * N, dtype=torch.int32).pin_memory()
+        import ctypes
+        arr = (ctypes.POINTER(ctypes.c_uint8) * nq)(
+            *[ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_uint8)) for t in h_q])
+        lens = np.array([len(q) for q in wl.queries], np.int32)
+        mat = np.ascontiguousarray(wl.matrix, np.int8)
+
+        def e2e_step():
+            s = sw.lib.sw_search_batch(db.handle, arr, lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       nq, mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                       wl.gap_open, wl.gap_extend,
+                                       ctypes.cast(h_s.data_ptr(), ctypes.POINTER(ctypes.c_int32)))
+            if s != 0:
+                raise RuntimeError(sw.sw_last_error())
+            return int(h_s[0])   # read of the step's result on the host
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * cells / dt / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": int(cat.size + mat.size),
+               "d2h_bytes_per_step": int(nq * N * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    f_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_gcups = sms * LANE_OPS_PER_CLK_SM * f_max * 2.0 / OPS_PER_CELL_PAIR / 1e9
+    st_last = sw.sw_get_stats(db)
+    inter_cells = st_last["inter_cells"]
+    k_ms = statistics.mean(inter_ms) if inter_ms else float("nan")
+    achieved = inter_cells / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
+                "frac": achieved / peak_gcups, "traffic": ncu_traffic(args.workload),
+                "kernel": INTER_KERNEL, "kernel_ms": k_ms,
+                "peak_basis": f"{sms} SMs x {LANE_OPS_PER_CLK_SM} int16x2 DPX lane-ops/clk x "
+                              f"{f_max / 1e6:.0f} MHz x 2 cells / {OPS_PER_CELL_PAIR} ops per "
+                              "cell pair (ALU issue bound; HBM is not the bound)",
+                "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks_source": peak_src}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (peak_gcups * clocks["sm_mhz"] * 1e6 / f_max)
+    line = {"metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int16x2 (int32 rescore)", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "queries": nq,
+                       "query_residues": int(cat.size), "db_seqs": N,
+                       "db_residues": wl.db.num_residues, "cells_per_step": cells,
+                       "per_gpu": "each rank searches its own database of this size",
+                       "l2": f"inputs larger than L2 (database {wl.db.num_residues / 1e6:.0f} MB "
+                             "resident in HBM, read once per query per step)"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+            "flagged_lanes_per_step": flagged / max(1, args.steps)}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(wl, args.cpu_seconds, args.seed)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    db.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

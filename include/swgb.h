@@ -1,0 +1,155 @@
+/*
+ * swgb -- Smith-Waterman protein database search on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libswgb.so.  Plain pointers and sizes only.
+ *
+ * What is computed (paper Section 2, Eqs. sw2-sw4): for a query S1 of length m and a
+ * database sequence S2 of length n,
+ *     H[i][j] = max{0, H[i-1][j-1] + SM(S1[i], S2[j]), E[i][j], F[i][j]}
+ *     E[i][j] = max{H[i][j-1] - Goe, E[i][j-1] - Ge}
+ *     F[i][j] = max{H[i-1][j] - Goe, F[i-1][j] - Ge}
+ * with H, E, F = 0 on row 0 and column 0; the score is max over i, j of H[i][j] (0 if m or
+ * n is 0).  One score per database sequence, one query against the whole database: the
+ * paper's inter-task database search (Sections 1 and 4).
+ *
+ * Gap costs: Goe = gap_open, Ge = gap_extend.  A gap of length k costs
+ * gap_open + (k - 1) * gap_extend (when gap_extend <= gap_open; otherwise Eqs. sw3/sw4
+ * charge each continuing position min(gap_open, gap_extend)).  The paper's own setting
+ * "open 10, extend 2" with Goe = open + extend is gap_open = 12, gap_extend = 2.
+ *
+ * Conventions shared by every call:
+ *  - Residues are codes in [0, alphabet_size), alphabet_size <= 32.  A code outside that
+ *    range is SW_ERR_CODE.
+ *  - The matrix is alphabet_size x alphabet_size int8, row-major, query letter first:
+ *    SM(a, b) = matrix[a * alphabet_size + b].
+ *  - gap_open >= 0, gap_extend >= 0, both <= 1,000,000.  Scores are int32; SW_ERR_ARG if
+ *    min(m, n) * max(SM) could exceed INT32_MAX.
+ *  - Zero-length queries and sequences are allowed and score 0.
+ *  - On a non-OK status no output is defined; sw_last_error() says why (thread-local).
+ *  - Host input buffers are borrowed for the duration of the call only.
+ *  - Calls on one database handle are serialised internally.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sw_db sw_db;          /* device-resident database, owned by the library */
+typedef struct sw_server sw_server;  /* continuous-batching search server */
+
+typedef enum {
+    SW_OK = 0,
+    SW_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad gap cost) */
+    SW_ERR_CODE = -2,     /* a residue code >= alphabet_size */
+    SW_ERR_OOM = -3,      /* device or host allocation failed */
+    SW_ERR_CUDA = -4,     /* a CUDA call failed (message in sw_last_error) */
+    SW_ERR_TIMEOUT = -5,  /* a bounded wait ran out */
+    SW_ERR_BUSY = -6,     /* server: no admission capacity for this request now */
+    SW_ERR_STATE = -7     /* call not valid in the object's current state */
+} sw_status;
+
+/* Options for sw_db_load_ex.  Zero fields take the defaults. */
+typedef struct {
+    int32_t device;        /* CUDA device ordinal (default: the current device) */
+    int32_t long_cutoff;   /* sequences longer than this go to the intra-task kernel
+                              (default 3072; must be a multiple of 8) */
+    int32_t flag_cap;      /* capacity of the list of saturated int16 lanes (default 2^20);
+                              when more lanes saturate, the rescore sweeps every score */
+    int32_t reserved[5];
+} sw_db_options;
+
+/* Per-call measurements of the last search on a handle (CUDA events on the launch stream). */
+typedef struct {
+    float inter_ms;        /* inter-task int16x2 kernel */
+    float intra_ms;        /* intra-task int32 kernel for long subjects */
+    float rescore_ms;      /* int32 rescore of saturated lanes */
+    float total_ms;        /* first to last launch of the search */
+    int64_t cells;         /* sum over queries of m * (database residues) */
+    int64_t inter_cells;   /* cells the inter-task kernel covered (real residues) */
+    int64_t flagged;       /* lanes that reached the int16 threshold and were rescored */
+    int64_t launches;      /* kernels launched by the search */
+    int32_t inter_grid;    /* persistent grid of the inter-task kernel (blocks) */
+    int32_t inter_block;   /* threads per block of the inter-task kernel */
+    int32_t graph_replay;  /* 1 if the launch sequence came from a CUDA graph */
+    int32_t reserved;
+} sw_stats;
+
+/* ---------------------------------------------------------------- database ------------ */
+
+/* Preprocessing stage (paper Section 4: sort by length ascending, pad with a dummy symbol,
+ * group by lane count).  Copies `residues[0 .. offsets[num_seqs])`, sequence k being
+ * residues[offsets[k] .. offsets[k+1]), to the device in a length-sorted, 64-sequence
+ * interleaved layout plus a plain copy.  offsets must start at 0 and be non-decreasing.
+ * The caller keeps its buffers; the handle is freed with sw_db_free. */
+sw_status sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t num_seqs,
+                     int32_t alphabet_size, sw_db **out);
+sw_status sw_db_load_ex(const uint8_t *residues, const int64_t *offsets, int64_t num_seqs,
+                        int32_t alphabet_size, const sw_db_options *opts, sw_db **out);
+void sw_db_free(sw_db *db);
+int64_t sw_db_num_seqs(const sw_db *db);
+int64_t sw_db_num_residues(const sw_db *db);
+
+/* ---------------------------------------------------------------- search -------------- */
+
+/* SW stage (paper Section 4) for one query: scores[k] = best local score of the query
+ * against database sequence k (original order).  Host query, host matrix, host output
+ * buffer of num_seqs int32.  Synchronous. */
+sw_status sw_search(const sw_db *db, const uint8_t *query, int32_t query_len,
+                    const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                    int32_t *scores);
+
+/* Several queries in one persistent launch.  queries[q] has query_lens[q] residues (host).
+ * scores is a host buffer of num_queries * num_seqs int32, row q = query q.  Synchronous. */
+sw_status sw_search_batch(const sw_db *db, const uint8_t *const *queries,
+                          const int32_t *query_lens, int32_t num_queries,
+                          const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                          int32_t *scores);
+
+/* Device-resident variant for callers that hold device memory (e.g. PyTorch tensors).
+ * d_queries: device buffer of concatenated query residues; query_offsets: HOST array of
+ * num_queries + 1 int64 offsets into it.  matrix: host.  d_scores: device buffer of
+ * num_queries * num_seqs int32.  Work is enqueued on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream); the call returns without waiting for it.  Repeated calls with
+ * the same shapes and pointers replay a captured CUDA graph. */
+sw_status sw_search_batch_device(const sw_db *db, const uint8_t *d_queries,
+                                 const int64_t *query_offsets, int32_t num_queries,
+                                 const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                                 int32_t *d_scores, void *stream);
+
+/* Measurements of the last completed search on `db` (synchronises the handle's stream). */
+sw_status sw_get_stats(const sw_db *db, sw_stats *out);
+
+/* ---------------------------------------------------------------- host-side plan ------ */
+
+/* Host-only view of the preprocessing stage, for inspection and tests (no GPU needed).
+ * sw_layout_sizes reports the sizes; sw_layout_build fills caller-owned buffers:
+ *   group_off[num_groups]   byte offset of each 64-sequence group in `inter`
+ *   group_len[num_groups]   padded column count of the group (multiple of 8)
+ *   perm[num_groups * 64]   original sequence id of each group slot, -1 for fillers
+ *   inter[inter_bytes]      interleaved residues: position j of slot s = 2t + l of group g
+ *                           is inter[group_off[g] + (j / 8) * 512 + t * 16 + (j % 8) * 2 + l],
+ *                           the dummy code alphabet_size past the end of the sequence
+ *   long_ids[num_long]      ids of sequences longer than long_cutoff, longest first
+ * Groups are in ascending length order. */
+sw_status sw_layout_sizes(const int64_t *offsets, int64_t num_seqs, int32_t long_cutoff,
+                          int64_t *num_groups, int64_t *inter_bytes, int64_t *num_long);
+sw_status sw_layout_build(const uint8_t *residues, const int64_t *offsets, int64_t num_seqs,
+                          int32_t alphabet_size, int32_t long_cutoff, int64_t *group_off,
+                          int32_t *group_len, int32_t *perm, uint8_t *inter,
+                          int32_t *long_ids);
+
+/* ---------------------------------------------------------------- misc ---------------- */
+
+const char *sw_last_error(void);      /* message for the last non-OK status (thread-local) */
+const char *sw_version(void);
+int64_t sw_launch_count(void);        /* kernels this library has launched (process-wide) */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_H */

@@ -1,0 +1,251 @@
+"""Smith-Waterman protein database search on NVIDIA GB300 (sm_103a).
+
+Thin ctypes binding over ``libswgb.so`` (C ABI in ``include/swgb.h``): argument marshalling
+only, every step of the search runs in the library's CUDA kernels.  There is no CPU path:
+if the library is missing or cannot be loaded, importing this package raises.
+
+Names follow the C ABI: ``sw_db_load``, ``sw_search``, ``sw_search_batch``,
+``sw_search_batch_device``, ``sw_get_stats``, ``sw_last_error``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"swgb status {status}: {msg}")
+        self.status = status
+
+
+STATUS = {0: "SW_OK", -1: "SW_ERR_ARG", -2: "SW_ERR_CODE", -3: "SW_ERR_OOM", -4: "SW_ERR_CUDA",
+          -5: "SW_ERR_TIMEOUT", -6: "SW_ERR_BUSY", -7: "SW_ERR_STATE"}
+
+
+class DbOptions(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("long_cutoff", ctypes.c_int32),
+                ("flag_cap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("inter_ms", ctypes.c_float), ("intra_ms", ctypes.c_float),
+                ("rescore_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("cells", ctypes.c_int64), ("inter_cells", ctypes.c_int64),
+                ("flagged", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("inter_grid", ctypes.c_int32), ("inter_block", ctypes.c_int32),
+                ("graph_replay", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libswgb.so not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python paper_1702_07195_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "sw_db_load": (ctypes.c_int, [_u8p, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_vp)]),
+        "sw_db_load_ex": (ctypes.c_int, [_u8p, _i64p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.POINTER(DbOptions), ctypes.POINTER(_vp)]),
+        "sw_db_free": (None, [_vp]),
+        "sw_db_num_seqs": (ctypes.c_int64, [_vp]),
+        "sw_db_num_residues": (ctypes.c_int64, [_vp]),
+        "sw_search": (ctypes.c_int, [_vp, _u8p, ctypes.c_int32, _i8p, ctypes.c_int32,
+                                     ctypes.c_int32, _i32p]),
+        "sw_search_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_u8p), _i32p, ctypes.c_int32, _i8p,
+                                           ctypes.c_int32, ctypes.c_int32, _i32p]),
+        "sw_search_batch_device": (ctypes.c_int, [_vp, _vp, _i64p, ctypes.c_int32, _i8p,
+                                                  ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+        "sw_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+        "sw_layout_sizes": (ctypes.c_int, [_i64p, ctypes.c_int64, ctypes.c_int32, _i64p, _i64p, _i64p]),
+        "sw_layout_build": (ctypes.c_int, [_u8p, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           _i64p, _i32p, _i32p, _u8p, _i32p]),
+        "sw_last_error": (ctypes.c_char_p, []),
+        "sw_version": (ctypes.c_char_p, []),
+        "sw_launch_count": (ctypes.c_int64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def sw_last_error() -> str:
+    return lib.sw_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise SwError(status, f"{STATUS.get(status, status)}: {sw_last_error()}")
+
+
+def _u8(a):
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    if a.size == 0:
+        a = np.zeros(1, dtype=np.uint8)[:0]
+    return a
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _matrix(matrix):
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    if m.ndim != 2 or m.shape[0] != m.shape[1]:
+        raise ValueError("matrix must be square (A x A)")
+    return m
+
+
+class Database:
+    """A database resident on the GPU (``sw_db``).  Free with ``close()`` or a ``with`` block."""
+
+    def __init__(self, handle, alphabet_size):
+        self._h = handle
+        self.alphabet_size = alphabet_size
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("database is closed")
+        return self._h
+
+    @property
+    def num_seqs(self) -> int:
+        return int(lib.sw_db_num_seqs(self.handle))
+
+    @property
+    def num_residues(self) -> int:
+        return int(lib.sw_db_num_residues(self.handle))
+
+    def close(self):
+        if self._h:
+            lib.sw_db_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sw_db_load(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 0,
+               device: int = 0, flag_cap: int = 0) -> Database:
+    """Preprocess and upload a database (residues uint8 codes, offsets int64[N+1])."""
+    r = _u8(residues)
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = int(o.shape[0] - 1)
+    opts = DbOptions()
+    opts.device = int(device)
+    opts.long_cutoff = int(long_cutoff)
+    opts.flag_cap = int(flag_cap)
+    h = _vp()
+    _check(lib.sw_db_load_ex(_ptr(r, _u8p), _ptr(o, _i64p), n, int(alphabet_size),
+                             ctypes.byref(opts), ctypes.byref(h)))
+    return Database(h, alphabet_size)
+
+
+def sw_search(db: Database, query, matrix, gap_open: int, gap_extend: int) -> np.ndarray:
+    """Scores of one query against every database sequence (int32, original order)."""
+    q = _u8(query)
+    m = _matrix(matrix)
+    out = np.empty(db.num_seqs, dtype=np.int32)
+    _check(lib.sw_search(db.handle, _ptr(q, _u8p), int(q.shape[0]), _ptr(m, _i8p), int(gap_open),
+                         int(gap_extend), _ptr(out, _i32p)))
+    return out
+
+
+def sw_search_batch(db: Database, queries, matrix, gap_open: int, gap_extend: int) -> np.ndarray:
+    """Scores of several queries, shape (num_queries, num_seqs), int32."""
+    qs = [_u8(q) for q in queries]
+    m = _matrix(matrix)
+    arr = (_u8p * max(1, len(qs)))(*[_ptr(q, _u8p) for q in qs])
+    lens = np.array([q.shape[0] for q in qs] or [0], dtype=np.int32)
+    out = np.empty((len(qs), db.num_seqs), dtype=np.int32)
+    _check(lib.sw_search_batch(db.handle, arr, _ptr(lens, _i32p), len(qs), _ptr(m, _i8p),
+                               int(gap_open), int(gap_extend), _ptr(out, _i32p)))
+    return out
+
+
+def sw_search_batch_device(db: Database, d_queries, query_offsets, matrix, gap_open: int,
+                           gap_extend: int, d_scores, stream=None) -> None:
+    """Device-resident batch search on torch CUDA tensors; enqueued on ``stream``.
+
+    d_queries: uint8 CUDA tensor of concatenated queries; query_offsets: host int64 array
+    (num_queries + 1); d_scores: int32 CUDA tensor of num_queries * num_seqs elements.
+    ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for torch's current stream.
+    """
+    import torch
+    o = np.ascontiguousarray(query_offsets, dtype=np.int64)
+    nq = int(o.shape[0] - 1)
+    if d_scores.dtype != torch.int32 or not d_scores.is_cuda or not d_scores.is_contiguous():
+        raise ValueError("d_scores must be a contiguous int32 CUDA tensor")
+    if d_scores.numel() < nq * db.num_seqs:
+        raise ValueError("d_scores too small")
+    if d_queries.dtype != torch.uint8 or not d_queries.is_cuda or not d_queries.is_contiguous():
+        raise ValueError("d_queries must be a contiguous uint8 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream(d_scores.device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    m = _matrix(matrix)
+    _check(lib.sw_search_batch_device(db.handle, _vp(d_queries.data_ptr()), _ptr(o, _i64p), nq,
+                                      _ptr(m, _i8p), int(gap_open), int(gap_extend),
+                                      _vp(d_scores.data_ptr()), _vp(s)))
+
+
+def sw_get_stats(db: Database) -> dict:
+    st = Stats()
+    _check(lib.sw_get_stats(db.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def sw_launch_count() -> int:
+    return int(lib.sw_launch_count())
+
+
+def sw_layout(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 3072) -> dict:
+    """Host-only preprocessing stage (no GPU): the interleaved layout the kernels read."""
+    r = _u8(residues)
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = int(o.shape[0] - 1)
+    ng, nb, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.sw_layout_sizes(_ptr(o, _i64p), n, int(long_cutoff), ctypes.byref(ng),
+                               ctypes.byref(nb), ctypes.byref(nl)))
+    goff = np.zeros(max(1, ng.value), np.int64)
+    glen = np.zeros(max(1, ng.value), np.int32)
+    perm = np.zeros(max(1, ng.value * 64), np.int32)
+    inter = np.zeros(max(1, nb.value), np.uint8)
+    lids = np.zeros(max(1, nl.value), np.int32)
+    _check(lib.sw_layout_build(_ptr(r, _u8p), _ptr(o, _i64p), n, int(alphabet_size),
+                               int(long_cutoff), _ptr(goff, _i64p), _ptr(glen, _i32p),
+                               _ptr(perm, _i32p), _ptr(inter, _u8p), _ptr(lids, _i32p)))
+    return {"group_off": goff[:ng.value], "group_len": glen[:ng.value],
+            "perm": perm[:ng.value * 64], "inter": inter[:nb.value], "long_ids": lids[:nl.value]}

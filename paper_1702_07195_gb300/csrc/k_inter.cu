@@ -1,0 +1,227 @@
+// Inter-task Smith-Waterman/Gotoh kernel: packed int16x2 lanes, Blackwell DPX max-plus ops.
+//
+// Paper Section 4 (inter-task scheme, Section 4.1 vertical blocking, Section 4.2 narrow
+// integer ranges with recomputation, Section 4.3 query profile), redesigned for sm_103a:
+//  * one warp aligns one query against a group of 64 database sequences: 32 threads, each
+//    holding two sequences in the two 16-bit halves of every register (int16x2 lanes);
+//  * the query is cut into strips of T rows ("vertical blocks"); a thread keeps the strip's
+//    H - Goe and E columns in registers and sweeps the whole subject, one column at a time;
+//    the strip's bottom row (H - Goe, F) goes to a per-warp global buffer that the next
+//    strip reads (coalesced 16-byte accesses, L2 resident for typical lengths);
+//  * the query profile for 256 rows at a time sits in shared memory; one 16-byte load
+//    serves 8 rows of one lane, and a byte permute packs the two lanes' scores;
+//  * the cell update is five DPX operations per cell pair plus half a three-way max for the
+//    running best (Eqs. sw2-sw4, rearranged as shown in `cell` below);
+//  * blocks are persistent and take (query, 4 groups) items from an atomic queue, longest
+//    items first (the paper's dynamic distribution to idle threads, Section 4.1);
+//  * a lane whose best score reaches 32767 - max(SM) may have wrapped and is flagged; its
+//    exact score comes from the int32 rescore kernel (Section 4.2's recomputation at the
+//    next wider range).  Below that threshold no intermediate can leave the int16 range.
+#include "swgb_device.cuh"
+
+namespace swgb {
+
+namespace {
+
+constexpr int kT = 32;          // query rows per strip (registers: 2 x kT)
+constexpr int kW = 4;           // warps per block = groups per work item
+constexpr int kBlock = kW * kWarp;
+
+struct Packed {
+    unsigned ngoe;   // (-Goe, -Goe)
+    unsigned nge;    // (-Ge, -Ge)
+    unsigned ngep;   // (-min(Ge, Goe), ...)
+    unsigned e0;     // E(i, 1) = -min(Ge, Goe): Eq. sw3 with the zero boundary
+    unsigned floor;  // (-32768, -32768)
+};
+
+__device__ __forceinline__ unsigned pack2(int v) {
+    return (static_cast<unsigned>(v) & 0xFFFFu) * 0x00010001u;
+}
+
+// One column of one strip for both lanes.
+//   diag : (H - Goe)(r0 - 1, j - 1)       f : F(r0, j)
+// returns, through hm_out / f, (H - Goe)(r_last, j) and F(r_last + 1, j).
+// Per row r with S' = SM + Goe from the profile:
+//   X      = max(Hm(r-1, j-1) + S', E(r, j), 0)        = max(0, H_diag + SM, E)    Eq. sw2 part
+//   H      = max(X, F(r, j))                            Eq. sw2
+//   Hm     = H - Goe = max(F - Goe, X - Goe)
+//   E(r, j+1) = max(E(r, j) - Ge, Hm)                   Eq. sw3
+//   F(r+1, j) = max(F - Ge, H - Goe) = max(F - min(Ge, Goe), X - Goe)   Eq. sw4
+//   best   = max(best, X)     (max H = max X: every F is bounded by an earlier X or by 0)
+__device__ __forceinline__ void column(unsigned (&Hm)[kT], unsigned (&E)[kT], unsigned& f,
+                                       unsigned& diag, const int16_t* qa, const int16_t* qb,
+                                       const Packed& k, unsigned& best) {
+    const uint4* pa = reinterpret_cast<const uint4*>(qa);
+    const uint4* pb = reinterpret_cast<const uint4*>(qb);
+    unsigned F = f;
+    unsigned d = diag;
+#pragma unroll
+    for (int r8 = 0; r8 < kT; r8 += 8) {
+        const uint4 a = pa[r8 >> 3];
+        const uint4 b = pb[r8 >> 3];
+        const unsigned wa[4] = {a.x, a.y, a.z, a.w};
+        const unsigned wb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = r8 + 2 * h;
+            const unsigned s0 = __byte_perm(wa[h], wb[h], 0x5410);   // row r:   (lane a, lane b)
+            const unsigned s1 = __byte_perm(wa[h], wb[h], 0x7632);   // row r+1
+            const unsigned x0 = __viaddmax_s16x2_relu(d, s0, E[r]);
+            const unsigned xm0 = __viaddmax_s16x2(x0, k.ngoe, k.floor);
+            d = Hm[r];
+            Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm0);
+            E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);
+            F = __viaddmax_s16x2(F, k.ngep, xm0);
+            const unsigned x1 = __viaddmax_s16x2_relu(d, s1, E[r + 1]);
+            const unsigned xm1 = __viaddmax_s16x2(x1, k.ngoe, k.floor);
+            d = Hm[r + 1];
+            Hm[r + 1] = __viaddmax_s16x2(F, k.ngoe, xm1);
+            E[r + 1] = __viaddmax_s16x2(E[r + 1], k.nge, Hm[r + 1]);
+            F = __viaddmax_s16x2(F, k.ngep, xm1);
+            best = __vimax3_s16x2(best, x0, x1);
+        }
+    }
+    f = F;
+}
+
+// One strip (query rows [s*kT, s*kT + kT)) of one group: sweeps all L columns.
+__device__ __forceinline__ void strip(const uint4* __restrict__ res, int L, uint4* bnd,
+                                      const int16_t* qp_strip, int qstride, bool first,
+                                      bool last, const Packed& k, unsigned& best, int lane) {
+    unsigned Hm[kT], E[kT];
+#pragma unroll
+    for (int r = 0; r < kT; ++r) {
+        Hm[r] = k.ngoe;   // H(r, 0) - Goe
+        E[r] = k.e0;      // E(r, 1)
+    }
+    const unsigned f_top = k.ngep;   // F(1, j) = max(0 - Goe, 0 - Ge) on the first strip
+    unsigned hm_prev = k.ngoe;       // (H - Goe)(r0 - 1, j - 1), column 0
+    uint4 w_next = res[lane];
+    uint4 b_next = first ? make_uint4(k.ngoe, f_top, k.ngoe, f_top) : bnd[lane];
+    for (int jc = 0; jc < L; jc += 8) {
+        const uint4 w = w_next;
+        if (jc + 8 < L) w_next = res[((jc >> 3) + 1) * kWarp + lane];
+        unsigned w0 = w.x, w1 = w.y, w2 = w.z, w3 = w.w;
+#pragma unroll 1
+        for (int h = 0; h < 4; ++h) {
+            const int j = jc + 2 * h;            // columns j and j + 1 (0-based)
+            const uint4 b = b_next;
+            if (!first && j + 2 < L) b_next = bnd[((j >> 1) + 1) * kWarp + lane];
+            // column j
+            unsigned f0 = b.y;
+            unsigned d0 = hm_prev;
+            column(Hm, E, f0, d0, qp_strip + (w0 & 0xFF) * qstride,
+                   qp_strip + ((w0 >> 8) & 0xFF) * qstride, k, best);
+            const unsigned out_hm0 = Hm[kT - 1];
+            // column j + 1
+            unsigned f1 = b.w;
+            unsigned d1 = b.x;
+            column(Hm, E, f1, d1, qp_strip + ((w0 >> 16) & 0xFF) * qstride,
+                   qp_strip + (w0 >> 24) * qstride, k, best);
+            hm_prev = b.z;
+            if (!last) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
+            w0 = w1;
+            w1 = w2;
+            w2 = w3;
+        }
+    }
+}
+
+__device__ __forceinline__ void emit(const InterParams& p, int q, int32_t* scores, int id, int v) {
+    if (id < 0) return;
+    if (v >= p.thresh) {
+        scores[id] = -1;
+        const unsigned slot = atomicAdd(&p.ctrl->flag_count, 1u);
+        if (slot < p.flag_cap) p.flags[slot] = FlagEntry{q, id};
+    } else {
+        scores[id] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_inter_i16x2(const InterParams p) {
+    extern __shared__ __align__(16) int16_t s_qp[];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warp = threadIdx.x >> 5;
+    const int qstride = kQpRows + kQpPad;
+    uint4* bnd = p.bnd + (static_cast<int64_t>(blockIdx.x) * kW + warp) * p.bnd_stride;
+    Packed k;
+    k.ngoe = pack2(-p.gaps.goe);
+    k.nge = pack2(-p.gaps.ge);
+    k.ngep = pack2(-p.gaps.gep);
+    k.e0 = pack2(-p.gaps.gep);
+    k.floor = 0x80008000u;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_inter, 1u));
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= p.num_items) break;
+        const InterItem item = p.items[it];
+        const QueryDesc qd = p.queries[item.query];
+        const bool active = warp < item.ngroups;
+        const int g = item.group + warp;
+        const int L = active ? p.group_len[g] : 0;
+        const uint4* res =
+            active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
+        const int S = (qd.m + kT - 1) / kT;
+        unsigned best = 0;
+        for (int c0 = 0; c0 < S * kT; c0 += kQpRows) {
+            __syncthreads();
+            constexpr int kVecPerRow = kQpRows / 8;
+            for (int v = threadIdx.x; v < p.alphabet1 * kVecPerRow; v += kBlock) {
+                const int d = v / kVecPerRow;
+                const int o = (v - d * kVecPerRow) * 8;
+                const uint4 x = *reinterpret_cast<const uint4*>(
+                    qd.qp + static_cast<int64_t>(d) * qd.m_pad + c0 + o);
+                *reinterpret_cast<uint4*>(s_qp + d * qstride + o) = x;
+            }
+            __syncthreads();
+            if (active && L > 0) {
+                const int s_end = min(S, (c0 + kQpRows) / kT);
+                for (int s = c0 / kT; s < s_end; ++s)
+                    strip(res, L, bnd, s_qp + (s * kT - c0), qstride, s == 0, s == S - 1, k,
+                          best, lane);
+            }
+        }
+        if (active) {
+            const int base = g * kGroupSeqs + 2 * lane;
+            const int b0 = static_cast<int>(static_cast<short>(best & 0xFFFFu));
+            const int b1 = static_cast<int>(static_cast<short>(best >> 16));
+            emit(p, item.query, qd.scores, p.perm[base], b0);
+            emit(p, item.query, qd.scores, p.perm[base + 1], b1);
+        }
+    }
+}
+
+}  // namespace
+
+int inter_block_threads() { return kBlock; }
+
+size_t inter_smem_bytes(int alphabet1) {
+    return static_cast<size_t>(alphabet1) * (kQpRows + kQpPad) * sizeof(int16_t);
+}
+
+int inter_occupancy(int alphabet1) {
+    int n = 0;
+    const size_t smem = inter_smem_bytes(alphabet1);
+    cudaFuncSetAttribute(k_inter_i16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_inter_i16x2, kBlock, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_inter(const InterParams& p, int grid, int block, cudaStream_t st) {
+    const size_t smem = inter_smem_bytes(p.alphabet1);
+    cudaError_t e = cudaFuncSetAttribute(k_inter_i16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_inter_i16x2<<<grid, block, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace swgb

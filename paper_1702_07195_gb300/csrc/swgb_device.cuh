@@ -1,0 +1,123 @@
+// Device-side data structures and launch entry points shared by the kernels and the host
+// runtime of libswgb.  Not part of the public C ABI (include/swgb.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swgb {
+
+constexpr int kWarp = 32;
+constexpr int kGroupSeqs = 64;     // sequences per interleaved group: 32 threads x 2 int16 lanes
+constexpr int kGroupChunk = 512;   // bytes per 8 columns of a group (32 threads x 16 B)
+constexpr int kQpRows = 256;       // query rows staged in shared memory per chunk; profiles are
+                                   // padded to a multiple of this
+constexpr int kQpPad = 8;          // int16 padding per shared-memory profile row (16 B)
+constexpr int kMaxAlphabet = 32;
+
+// One query of a search.  The profile is biased by the gap-open cost so that the int16x2
+// update can keep H - Goe instead of H (one DPX operation less per cell pair):
+//   qp[d * m_pad + i] = SM(q_i, d) + bias   for d < A, i < m
+//   qp[d * m_pad + i] = 0 + bias            for the dummy code d = A, or i >= m
+// with bias = Goe whenever Goe + 127 fits int16 (always on the int16x2 path); otherwise
+// bias = 0 and the int32 kernel adds Goe itself.
+// A score of 0 for the dummy code and the padded rows leaves every score unchanged (cells
+// there are bounded by cells of the real matrix).
+struct QueryDesc {
+    const int16_t* qp;
+    int32_t* scores;     // output row, indexed by original database sequence id
+    int32_t m;
+    int32_t m_pad;
+};
+
+// Block-level work item of the inter-task kernel: `ngroups` (<= warps per block) consecutive
+// groups starting at `group`, all against query slot `query`.
+struct InterItem {
+    int32_t query;
+    int32_t group;
+    int32_t ngroups;
+    int32_t cost;        // unused on the device; the host sorts by it
+};
+
+struct FlagEntry {
+    int32_t query;
+    int32_t seq;
+};
+
+// Zeroed before every launch sequence.
+struct Control {
+    unsigned long long next_intra;   // intra-task pair counter
+    unsigned long long sweep_next;   // rescore sweep block counter
+    unsigned int next_inter;         // inter-task item counter
+    unsigned int next_rescore;       // saturation-list counter
+    unsigned int flag_count;         // saturated lanes seen by the inter-task kernel
+    unsigned int status;             // bit 0: a query residue code was out of range
+};
+
+struct Gaps {
+    int32_t goe;         // Goe
+    int32_t ge;          // Ge
+    int32_t gep;         // min(Ge, Goe): the cost a continuing F position pays in Eq. sw4
+};
+
+struct InterParams {
+    const uint8_t* inter;
+    const int64_t* group_off;
+    const int32_t* group_len;
+    const int32_t* perm;
+    const QueryDesc* queries;
+    const InterItem* items;
+    int32_t num_items;
+    int32_t alphabet1;   // A + 1 profile rows (the last is the dummy code)
+    Control* ctrl;
+    FlagEntry* flags;
+    uint32_t flag_cap;
+    int32_t thresh;      // int16 saturation threshold: 32767 - max(0, max SM)
+    uint4* bnd;          // strip-boundary buffers, one per resident warp
+    int64_t bnd_stride;  // uint4 per warp slot
+    Gaps gaps;
+};
+
+// Work source of the int32 intra-task kernel.
+enum IntraMode : int32_t {
+    kIntraLong = 0,      // (query, long subject) pairs: num_queries x num_long
+    kIntraRescore = 1,   // entries of the saturation list, then a sweep if it overflowed
+    kIntraAll = 2        // every (query, sequence) pair (int16 path not applicable)
+};
+
+struct IntraParams {
+    const uint8_t* plain;       // all sequences, original order
+    const int64_t* plain_off;
+    const QueryDesc* queries;
+    int32_t num_queries;
+    int32_t mode;
+    const int32_t* long_ids;    // kIntraLong: subject ids, longest first
+    int64_t num_long;
+    const int32_t* query_order; // query slots, longest first
+    int64_t num_seqs;
+    const FlagEntry* flags;
+    uint32_t flag_cap;
+    int32_t alphabet1;
+    Control* ctrl;
+    int2* spill;                // per resident warp: (H - Goe, F) of the pass boundary row
+    int64_t spill_stride;       // int2 per warp slot
+    Gaps gaps;
+    int32_t qp_add;             // Goe minus the profile's bias (0 unless Goe is too large)
+};
+
+// Launchers (return the CUDA error of the launch).
+cudaError_t launch_build_qp(const uint8_t* d_queries, const int64_t* d_qoff, int32_t nq,
+                            const int8_t* d_matrix, int32_t A, int32_t bias,
+                            const int64_t* d_qp_off, const int32_t* d_mpad, int16_t* d_qp,
+                            int64_t max_mpad, Control* ctrl, cudaStream_t st);
+cudaError_t launch_inter(const InterParams& p, int grid, int block, cudaStream_t st);
+int inter_block_threads();
+size_t inter_smem_bytes(int alphabet1);
+int inter_occupancy(int alphabet1);
+cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
+int intra_block_threads();
+int intra_rows_per_pass();
+size_t intra_smem_bytes(int alphabet1);
+int intra_occupancy(int alphabet1);
+
+}  // namespace swgb

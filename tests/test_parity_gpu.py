@@ -1,0 +1,214 @@
+"""GPU parity: every score from the CUDA path (through the C ABI) equals the CPU oracle's,
+bit for bit (integer arithmetic: tolerance 0).
+
+Sizes span several 64-sequence groups, 32-row strips, 256-row profile chunks and ragged
+tails; edge cases cover empty inputs, length-1 inputs, gap-cost regimes (including
+Goe < Ge and costs too large for the int16 path), asymmetric matrices, planted hits that
+saturate int16 lanes (exact int32 rescore, Section 4.2), the rescore sweep when the
+saturation list overflows, and subjects routed to the intra-task kernel.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_lib()
+    import paper_1702_07195_gb300 as m
+    return m
+
+
+def _oracle_all(queries, db, matrix, goe, ge):
+    return np.stack([oracle.sw_search(q, db.residues, db.offsets, matrix, goe, ge)[0]
+                     for q in queries]) if len(queries) else np.zeros((0, db.num_seqs), np.int64)
+
+
+def _check(got, exp, what=""):
+    got = np.asarray(got, dtype=np.int64)
+    assert got.shape == exp.shape, (got.shape, exp.shape)
+    bad = np.argwhere(got != exp)
+    if bad.size:
+        i = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches; first at {i}: gpu {got[i]} oracle {exp[i]}")
+
+
+def test_plain_reduced(sw):
+    wl = w.plain(seed=1, scale=0.2)                      # 2,000 sequences, m = 144
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as db:
+        got = sw.sw_search(db, wl.queries[0], wl.matrix, wl.gap_open, wl.gap_extend)
+        st = sw.sw_get_stats(db)
+    _check(got[None], _oracle_all(wl.queries, wl.db, wl.matrix, 10, 2), "plain")
+    assert st["cells"] == 144 * wl.db.num_residues and st["inter_ms"] > 0
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 31, 32, 33, 63, 64, 65, 255, 256, 257, 300, 513])
+def test_query_lengths_around_tiles(sw, m):
+    rng = np.random.default_rng(m)
+    lens = np.concatenate([rng.integers(1, 400, size=133), [1, 2, 7, 8, 9, 15, 16, 17, 0]])
+    db = w.database_from_lengths(rng, lens)
+    q = w.draw_residues(rng, m)
+    sm = w.blosum62()
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search(h, q, sm, 10, 2)
+    _check(got[None], _oracle_all([q], db, sm, 10, 2), f"m={m}")
+
+
+@pytest.mark.parametrize("goe,ge", [(10, 2), (12, 2), (0, 0), (3, 7), (5, 0), (1, 1), (40, 1),
+                                    (16383, 16383), (20000, 3), (500000, 1)])
+def test_gap_regimes(sw, goe, ge):
+    rng = np.random.default_rng(goe * 7 + ge)
+    db = w.database_from_lengths(rng, rng.integers(0, 200, size=150))
+    qs = [w.draw_residues(rng, 90), w.draw_residues(rng, 37)]
+    sm = w.blosum62()
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search_batch(h, qs, sm, goe, ge)
+    _check(got, _oracle_all(qs, db, sm, goe, ge), f"gaps {goe},{ge}")
+
+
+def test_asymmetric_matrix_and_small_alphabet(sw):
+    rng = np.random.default_rng(42)
+    A = 5
+    sm = rng.integers(-6, 12, size=(A, A)).astype(np.int8)
+    lens = rng.integers(0, 120, size=200)
+    offs = np.zeros(201, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    db = w.Database(rng.integers(0, A, size=int(offs[-1])).astype(np.uint8), offs)
+    qs = [rng.integers(0, A, size=n).astype(np.uint8) for n in (70, 5, 33)]
+    with sw.sw_db_load(db.residues, db.offsets, A) as h:
+        got = sw.sw_search_batch(h, qs, sm, 4, 1)
+    _check(got, _oracle_all(qs, db, sm, 4, 1), "asymmetric")
+
+
+def test_empty_query_and_sequences(sw):
+    rng = np.random.default_rng(3)
+    db = w.database_from_lengths(rng, [0, 5, 0, 17, 1, 0])
+    sm = w.blosum62()
+    q = w.draw_residues(rng, 12)
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search_batch(h, [np.zeros(0, np.uint8), q], sm, 10, 2)
+    assert (got[0] == 0).all()
+    _check(got[1:], _oracle_all([q], db, sm, 10, 2), "empty")
+
+
+def test_single_sequence_database(sw):
+    rng = np.random.default_rng(4)
+    db = w.database_from_lengths(rng, [77])
+    q = w.draw_residues(rng, 50)
+    sm = w.blosum62()
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search(h, q, sm, 10, 2)
+    _check(got[None], _oracle_all([q], db, sm, 10, 2), "single")
+
+
+def test_empty_database(sw):
+    with sw.sw_db_load(np.zeros(0, np.uint8), np.array([0], np.int64), 24) as h:
+        got = sw.sw_search(h, w.encode("MKV"), w.blosum62(), 10, 2)
+    assert got.shape == (0,)
+
+
+@pytest.mark.parametrize("flag_cap", [0, 2, 1])
+def test_saturating_hits_rescored_exactly(sw, flag_cap):
+    """Planted hits above the int16 range go through the inter-task kernel (cutoff 8192),
+    are flagged and rescored in int32; flag_cap 1 and 2 overflow the saturation list and
+    exercise the sweep over all scores."""
+    wl = w.plain(seed=2, scale=0.05)
+    db2, q2, idx = w.plant_saturating(wl.db, wl.queries[0], count=6, run=3200)
+    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, long_cutoff=8192,
+                       flag_cap=flag_cap) as h:
+        got = sw.sw_search_batch(h, [q2, q2[:100], q2[-3300:]], wl.matrix, 10, 2)
+        st = sw.sw_get_stats(h)
+    exp = _oracle_all([q2, q2[:100], q2[-3300:]], db2, wl.matrix, 10, 2)
+    _check(got, exp, "saturating")
+    assert exp[0][idx].max() > 32767 and st["flagged"] >= 6
+
+
+def test_long_subjects_intra_kernel(sw):
+    rng = np.random.default_rng(9)
+    lens = np.concatenate([rng.integers(1, 300, size=120), rng.integers(1000, 2600, size=9), [4097]])
+    db = w.database_from_lengths(rng, lens)
+    qs = [w.draw_residues(rng, n) for n in (300, 1, 700)]
+    sm = w.blosum62()
+    exp = _oracle_all(qs, db, sm, 10, 2)
+    for cutoff in (64, 512, 8192):
+        with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE, long_cutoff=cutoff) as h:
+            got = sw.sw_search_batch(h, qs, sm, 10, 2)
+        _check(got, exp, f"cutoff {cutoff}")
+
+
+def test_long_subject_saturation(sw):
+    """A long subject (intra-task int32 path) with a hit far above the int16 range."""
+    run = np.full(4000, w.CODE_W, np.uint8)
+    db = w.from_sequences([run, w.encode("WWWW"), run[:100]])
+    q = np.concatenate([w.encode("MK"), run[:3500]])
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE, long_cutoff=512) as h:
+        got = sw.sw_search(h, q, w.blosum62(), 10, 2)
+    assert got.tolist() == [3500 * 11, 44, 1100]
+
+
+def test_batched_many_queries(sw):
+    wl = w.batched(seed=5, scale=0.002, query_lengths=[144, 211, 375, 807, 1434])
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search_batch(h, wl.queries, wl.matrix, 10, 2)
+    _check(got, _oracle_all(wl.queries, wl.db, wl.matrix, 10, 2), "batched")
+
+
+def test_device_api_torch_stream(sw):
+    import torch
+    wl = w.plain(seed=6, scale=0.03)
+    qs = [wl.queries[0], wl.queries[0][:50]]
+    cat = np.concatenate(qs)
+    offs = np.array([0, len(qs[0]), len(cat)], np.int64)
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        dq = torch.from_numpy(cat).cuda()
+        out = torch.full((2 * h.num_seqs,), -7, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            sw.sw_search_batch_device(h, dq, offs, wl.matrix, 10, 2, out, stream=s)
+        s.synchronize()
+        got = out.cpu().numpy().reshape(2, -1)
+        # a repeated call with the same shapes and pointers
+        out.fill_(-7)
+        sw.sw_search_batch_device(h, dq, offs, wl.matrix, 10, 2, out)
+        torch.cuda.synchronize()
+        got2 = out.cpu().numpy().reshape(2, -1)
+    exp = _oracle_all(qs, wl.db, wl.matrix, 10, 2)
+    _check(got, exp, "device api")
+    _check(got2, exp, "device api repeat")
+
+
+def test_errors_are_reported(sw):
+    rng = np.random.default_rng(1)
+    db = w.database_from_lengths(rng, [10, 20])
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_search(h, np.array([1, 2, 99], np.uint8), w.blosum62(), 10, 2)
+        assert e.value.status == -2
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_search(h, np.array([1, 2], np.uint8), w.blosum62(), -1, 2)
+        assert e.value.status == -1
+        ok = sw.sw_search(h, w.draw_residues(rng, 30), w.blosum62(), 10, 2)
+        assert ok.shape == (2,)
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_db_load(np.array([0, 50], np.uint8), np.array([0, 2], np.int64), 24)
+    assert e.value.status == -2
+
+
+def test_results_independent_of_routing(sw):
+    """Same scores whatever the inter/intra cutoff (property at any size)."""
+    wl = w.plain(seed=8, scale=0.1)
+    outs = []
+    for cutoff in (128, 256, 3072):
+        with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE, long_cutoff=cutoff) as h:
+            outs.append(sw.sw_search(h, wl.queries[0], wl.matrix, 10, 2))
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
