@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain", "paper_shaped", "long_subject"])
     ap.add_argument("--scale", type=float, default=1.0, help="database scale (tests only)")
+    ap.add_argument("--query-lengths", default="",
+                    help="comma-separated query lengths replacing the workload's (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -73,7 +75,10 @@ WORKLOAD_TEXT = {
 }
 
 
-def make_workload(name, seed, scale):
+def make_workload(name, seed, scale, query_lengths=""):
+    if query_lengths:
+        ql = [int(x) for x in query_lengths.split(",") if x]
+        return getattr(w, name)(seed=seed, scale=scale, query_lengths=ql)
     return getattr(w, name)(seed=seed, scale=scale)
 
 
@@ -198,7 +203,7 @@ def cpu_baseline(wl, seconds, seed):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    wl = make_workload(args.workload, args.seed, args.scale)
+    wl = make_workload(args.workload, args.seed, args.scale, args.query_lengths)
     vals = []
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     cb = None
@@ -231,7 +236,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    wl = make_workload(args.workload, args.seed + rank, args.scale)
+    wl = make_workload(args.workload, args.seed + rank, args.scale, args.query_lengths)
     nq = len(wl.queries)
     cat = np.concatenate(wl.queries)
     qoff = np.zeros(nq + 1, np.int64)

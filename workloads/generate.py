@@ -138,10 +138,11 @@ class Workload:
 
 
 # Configurations.  ``scale`` shrinks the database (number of sequences) for parity tests.
-def plain(seed=0, scale=1.0) -> Workload:
+def plain(seed=0, scale=1.0, query_lengths=None) -> Workload:
     """One 144-residue query vs 10,000 sequences (log-normal mean 250, clip 20..2000)."""
     db = make_database(max(1, int(10_000 * scale)), 250.0, 0.8, 20, 2000, seed=seed)
-    return Workload("plain", make_queries([144], seed), db, blosum62())
+    ql = [144] if query_lengths is None else query_lengths
+    return Workload("plain", make_queries(ql, seed), db, blosum62())
 
 
 def batched(seed=0, scale=1.0, query_lengths=None) -> Workload:
