@@ -142,6 +142,40 @@ sw_status sw_layout_build(const uint8_t *residues, const int64_t *offsets, int64
                           int32_t *group_len, int32_t *perm, uint8_t *inter,
                           int32_t *long_ids);
 
+/* ---------------------------------------------------------------- no device allocation */
+
+/* The paper has no counterpart to this entry point; it exists for callers that cannot let a
+ * library allocate device memory at search time.  The other search calls grow a per-database
+ * workspace with cudaMalloc when a larger search arrives.  That does not suit a service that
+ * overlaps many streams (cudaMalloc/cudaFree may synchronise the whole device), a process
+ * whose device memory is already handed out by another allocator (a framework's caching
+ * allocator, a pool sized at start-up, a container with a hard limit), or code that must not
+ * allocate after initialisation.
+ *
+ * sw_search_noalloc scores one query against every database sequence, like
+ * sw_search_batch_device with num_queries = 1, and calls no allocation routine: all its
+ * working memory lives in one fixed array of SW_NOALLOC_SCRATCH_BYTES (about 85 MiB) inside
+ * the library's device image.  That array is held on every device where this entry point
+ * runs until the process exits.  The first call on a device resolves the array's address
+ * there (with that device current); make that first call before any stream capture.
+ *   d_query   device buffer of query_len residue codes (each < alphabet_size; an
+ *             out-of-range code is scored as 0)
+ *   matrix    host, alphabet_size x alphabet_size int8 (copied before the call returns)
+ *   d_scores  device buffer of sw_db_num_seqs(db) int32, original database order
+ *   stream    cudaStream_t (NULL = legacy default stream); the call only enqueues work.
+ * Limits: query_len <= SW_NOALLOC_MAX_QUERY; a database whose groups or sequences are too
+ * long for the fixed boundary buffers, or with more than 2^20 groups, is rejected with
+ * SW_ERR_ARG.  The boundary buffers bound the number of resident blocks, so large databases
+ * search more slowly than with sw_search_batch_device.
+ * Every call shares the one array: calls whose work overlaps on the GPU (different streams,
+ * or different host threads without ordering) race and give undefined scores.  Serialise
+ * them, e.g. on one stream. */
+#define SW_NOALLOC_MAX_QUERY 8192
+#define SW_NOALLOC_SCRATCH_BYTES 89147904
+sw_status sw_search_noalloc(const sw_db *db, const uint8_t *d_query, int32_t query_len,
+                            const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                            int32_t *d_scores, void *stream);
+
 /* ---------------------------------------------------------------- misc ---------------- */
 
 const char *sw_last_error(void);      /* message for the last non-OK status (thread-local) */

@@ -74,6 +74,8 @@ def _load():
         "sw_search_batch_device": (ctypes.c_int, [_vp, _vp, _i64p, ctypes.c_int32, _i8p,
                                                   ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
         "sw_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+        "sw_search_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _i8p, ctypes.c_int32,
+                                             ctypes.c_int32, _vp, _vp]),
         "sw_layout_sizes": (ctypes.c_int, [_i64p, ctypes.c_int64, ctypes.c_int32, _i64p, _i64p, _i64p]),
         "sw_layout_build": (ctypes.c_int, [_u8p, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            _i64p, _i32p, _i32p, _u8p, _i32p]),
@@ -219,6 +221,30 @@ def sw_search_batch_device(db: Database, d_queries, query_offsets, matrix, gap_o
     _check(lib.sw_search_batch_device(db.handle, _vp(d_queries.data_ptr()), _ptr(o, _i64p), nq,
                                       _ptr(m, _i8p), int(gap_open), int(gap_extend),
                                       _vp(d_scores.data_ptr()), _vp(s)))
+
+
+def sw_search_noalloc(db: Database, d_query, matrix, gap_open: int, gap_extend: int, d_scores,
+                      stream=None) -> None:
+    """One query, no device allocation inside the library (see include/swgb.h).
+
+    For callers that cannot let a library call cudaMalloc at search time.  d_query: uint8
+    CUDA tensor; d_scores: int32 CUDA tensor of num_seqs elements.  Calls that overlap on the
+    GPU share one fixed scratch array and race: keep them on one stream.
+    """
+    import torch
+    if d_scores.dtype != torch.int32 or not d_scores.is_cuda or not d_scores.is_contiguous():
+        raise ValueError("d_scores must be a contiguous int32 CUDA tensor")
+    if d_scores.numel() < db.num_seqs:
+        raise ValueError("d_scores too small")
+    if d_query.dtype != torch.uint8 or not d_query.is_cuda or not d_query.is_contiguous():
+        raise ValueError("d_query must be a contiguous uint8 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream(d_scores.device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    m = _matrix(matrix)
+    _check(lib.sw_search_noalloc(db.handle, _vp(d_query.data_ptr()), int(d_query.numel()),
+                                 _ptr(m, _i8p), int(gap_open), int(gap_extend),
+                                 _vp(d_scores.data_ptr()), _vp(s)))
 
 
 def sw_get_stats(db: Database) -> dict:

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/swgb.h"
+#include "db_view.h"
 #include "layout.h"
 #include "swgb_device.cuh"
 
@@ -578,3 +579,39 @@ sw_status sw_get_stats(const sw_db* cdb, sw_stats* out) {
 }
 
 }  // extern "C"
+
+// ================================================================= internal accessors
+// Read-only view of a loaded database for other translation units of the library.
+
+namespace swgb {
+
+bool db_view(const sw_db* db, DbView* v) {
+    if (!db || !v) return false;
+    v->device = db->device;
+    v->sms = db->sms;
+    v->alphabet = db->A;
+    v->num_seqs = db->layout.num_seqs;
+    v->num_residues = db->num_residues;
+    v->short_residues = db->layout.short_residues;
+    v->num_groups = db->layout.num_groups;
+    v->max_group_len = db->layout.max_group_len;
+    v->max_len = db->layout.max_len;
+    v->num_long = static_cast<int64_t>(db->layout.long_ids.size());
+    v->flag_cap = db->flag_cap;
+    v->inter_occ = db->inter_occ;
+    v->intra_occ = db->intra_occ;
+    v->inter = db->inter.ptr;
+    v->group_off = db->group_off.ptr;
+    v->group_len = db->group_len.ptr;
+    v->perm = db->perm.ptr;
+    v->plain = db->plain.ptr;
+    v->plain_off = db->plain_off.ptr;
+    v->long_ids = db->long_ids.ptr;
+    return true;
+}
+
+sw_status set_last_error(sw_status st, const char* msg) { return fail(st, "%s", msg); }
+
+void add_launches(int64_t n) { g_launches += n; }
+
+}  // namespace swgb
