@@ -35,11 +35,13 @@ sys.path.insert(0, ROOT)
 
 import workloads as w  # noqa: E402
 
-# Issue-rate roofline of the inter-task kernel (derivation in the design doc): 128 int16x2 DPX
-# lane-operations per clock per SM (measured), two cells per lane-operation, and 6.5 issued
-# operations per cell pair (5 DPX updates + 0.5 three-way max + 1 byte permute).
-LANE_OPS_PER_CLK_SM = 128
-OPS_PER_CELL_PAIR = 6.5
+# ALU-pipe roofline of the inter-task kernel (derivation in the design doc): the DPX max-plus
+# operations issue on the ALU pipe at 64 lane-operations per clock per SM (ncu: the pipe is
+# 92% busy at 0.52 IPC per sub-partition; wall-clock probe: 18.9e12 lane-ops/s at 2,070 MHz
+# on 152 SMs), two cells per int16x2 lane-operation, and at least 5.5 ALU operations per cell
+# pair for Eqs. sw2-sw4 (5 DPX updates + half a three-way max for the running best).
+LANE_OPS_PER_CLK_SM = 64
+OPS_PER_CELL_PAIR = 5.5
 INTER_KERNEL = "k_inter_i16x2"
 INTER_SRC = os.path.join(ROOT, "paper_1702_07195_gb300", "csrc", "k_inter.cu")
 
@@ -60,6 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner")
     return ap.parse_args()
 
 
@@ -248,6 +251,12 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     cells = int(cat.size) * wl.db.num_residues
 
+    tune = None
+    if not args.no_tune:
+        # probe: the median-length query against the whole database, every kernel variant
+        probe = sorted(wl.queries, key=len)[len(wl.queries) // 2]
+        tune = sw.sw_db_tune(db, [probe], wl.matrix, wl.gap_open, wl.gap_extend)
+
     def step():
         sw.sw_search_batch_device(db, d_q, qoff, wl.matrix, wl.gap_open, wl.gap_extend, d_s,
                                   stream=stream)
@@ -337,9 +346,9 @@ def run_ours(args, world, rank, local):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
                 "frac": achieved / peak_gcups, "traffic": ncu_traffic(args.workload),
                 "kernel": INTER_KERNEL, "kernel_ms": k_ms,
-                "peak_basis": f"{sms} SMs x {LANE_OPS_PER_CLK_SM} int16x2 DPX lane-ops/clk x "
-                              f"{f_max / 1e6:.0f} MHz x 2 cells / {OPS_PER_CELL_PAIR} ops per "
-                              "cell pair (ALU issue bound; HBM is not the bound)",
+                "peak_basis": f"{sms} SMs x {LANE_OPS_PER_CLK_SM} ALU-pipe int16x2 lane-ops/clk x "
+                              f"{f_max / 1e6:.0f} MHz x 2 cells / {OPS_PER_CELL_PAIR} DPX ops per "
+                              "cell pair (ALU-pipe bound; HBM is not the bound)",
                 "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks_source": peak_src}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (peak_gcups * clocks["sm_mhz"] * 1e6 / f_max)
@@ -350,6 +359,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD_TEXT[args.workload], "queries": nq,
                        "query_residues": int(cat.size), "db_seqs": N,
                        "db_residues": wl.db.num_residues, "cells_per_step": cells,
+                       "kernel_variant": tune,
                        "per_gpu": "each rank searches its own database of this size",
                        "l2": f"inputs larger than L2 (database {wl.db.num_residues / 1e6:.0f} MB "
                              "resident in HBM, read once per query per step)"},

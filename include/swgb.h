@@ -74,8 +74,8 @@ typedef struct {
     int64_t launches;      /* kernels launched by the search */
     int32_t inter_grid;    /* persistent grid of the inter-task kernel (blocks) */
     int32_t inter_block;   /* threads per block of the inter-task kernel */
-    int32_t graph_replay;  /* 1 if the launch sequence came from a CUDA graph */
-    int32_t reserved;
+    int32_t graph_replay;  /* 1 if the launch sequence was a replayed CUDA graph */
+    int32_t variant;       /* inter-task kernel variant used (see sw_db_tune) */
 } sw_stats;
 
 /* ---------------------------------------------------------------- database ------------ */
@@ -119,6 +119,30 @@ sw_status sw_search_batch_device(const sw_db *db, const uint8_t *d_queries,
                                  const int64_t *query_offsets, int32_t num_queries,
                                  const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                                  int32_t *d_scores, void *stream);
+
+/* Autotuner.  The inter-task kernel comes in variants (query rows per strip x warps per
+ * block, e.g. 32x4, 64x4, 32x8, 64x8: registers vs. occupancy vs. per-column overhead).
+ * sw_db_tune runs the given probe queries (host) against the whole database once per variant
+ * (after one warm-up run), times the inter-task kernel with CUDA events, and makes the fastest
+ * variant the one every later search on `db` uses.  If `cache_path` is non-NULL the choice is
+ * looked up there first (key: device name, SM count, alphabet size, database shape, probe
+ * length class) and stored there after tuning; with `force` the cache is ignored on lookup.
+ * The paper tunes by hand (thread counts, Section 5.2); it has no autotuner. */
+typedef struct {
+    int32_t variant;             /* chosen variant index */
+    int32_t rows_per_strip;      /* its query rows per strip */
+    int32_t warps_per_block;     /* its warps per block */
+    int32_t from_cache;          /* 1 if taken from the cache without timing */
+    int32_t num_variants;
+    float gcups[8];              /* inter-task kernel GCUPS per variant (0 = not run) */
+} sw_tune_result;
+sw_status sw_db_tune(sw_db *db, const uint8_t *const *queries, const int32_t *query_lens,
+                     int32_t num_queries, const int8_t *matrix, int32_t gap_open,
+                     int32_t gap_extend, const char *cache_path, int32_t force,
+                     sw_tune_result *out);
+
+/* Selects an inter-task kernel variant directly (-1 restores the default). */
+sw_status sw_db_set_variant(sw_db *db, int32_t variant);
 
 /* Measurements of the last completed search on `db` (synchronises the handle's stream). */
 sw_status sw_get_stats(const sw_db *db, sw_stats *out);

@@ -42,10 +42,21 @@ class Stats(ctypes.Structure):
                 ("cells", ctypes.c_int64), ("inter_cells", ctypes.c_int64),
                 ("flagged", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("inter_grid", ctypes.c_int32), ("inter_block", ctypes.c_int32),
-                ("graph_replay", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_replay", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("rows_per_strip", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("num_variants", ctypes.c_int32), ("gcups", ctypes.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        return {"variant": self.variant, "rows_per_strip": self.rows_per_strip,
+                "warps_per_block": self.warps_per_block, "from_cache": bool(self.from_cache),
+                "gcups": [round(float(x), 1) for x in self.gcups[:self.num_variants]]}
 
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -79,6 +90,10 @@ def _load():
         "sw_layout_sizes": (ctypes.c_int, [_i64p, ctypes.c_int64, ctypes.c_int32, _i64p, _i64p, _i64p]),
         "sw_layout_build": (ctypes.c_int, [_u8p, _i64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            _i64p, _i32p, _i32p, _u8p, _i32p]),
+        "sw_db_tune": (ctypes.c_int, [_vp, ctypes.POINTER(_u8p), _i32p, ctypes.c_int32, _i8p,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                                      ctypes.c_int32, ctypes.POINTER(TuneResult)]),
+        "sw_db_set_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
         "sw_last_error": (ctypes.c_char_p, []),
         "sw_version": (ctypes.c_char_p, []),
         "sw_launch_count": (ctypes.c_int64, []),
@@ -245,6 +260,25 @@ def sw_search_noalloc(db: Database, d_query, matrix, gap_open: int, gap_extend: 
     _check(lib.sw_search_noalloc(db.handle, _vp(d_query.data_ptr()), int(d_query.numel()),
                                  _ptr(m, _i8p), int(gap_open), int(gap_extend),
                                  _vp(d_scores.data_ptr()), _vp(s)))
+
+
+def sw_db_tune(db: Database, queries, matrix, gap_open: int, gap_extend: int,
+               cache_path: str | None = None, force: bool = False) -> dict:
+    """Times every inter-task kernel variant on the probe queries and keeps the fastest."""
+    qs = [_u8(q) for q in queries]
+    m = _matrix(matrix)
+    arr = (_u8p * max(1, len(qs)))(*[_ptr(q, _u8p) for q in qs])
+    lens = np.array([q.shape[0] for q in qs] or [0], dtype=np.int32)
+    res = TuneResult()
+    _check(lib.sw_db_tune(db.handle, arr, _ptr(lens, _i32p), len(qs), _ptr(m, _i8p),
+                          int(gap_open), int(gap_extend),
+                          cache_path.encode() if cache_path else None, int(force),
+                          ctypes.byref(res)))
+    return res.as_dict()
+
+
+def sw_db_set_variant(db: Database, variant: int) -> None:
+    _check(lib.sw_db_set_variant(db.handle, int(variant)))
 
 
 def sw_get_stats(db: Database) -> dict:

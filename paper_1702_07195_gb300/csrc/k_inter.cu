@@ -23,9 +23,6 @@ namespace swgb {
 
 namespace {
 
-constexpr int kT = 32;          // query rows per strip (registers: 2 x kT)
-constexpr int kW = 4;           // warps per block = groups per work item
-constexpr int kBlock = kW * kWarp;
 
 struct Packed {
     unsigned ngoe;   // (-Goe, -Goe)
@@ -39,7 +36,7 @@ __device__ __forceinline__ unsigned pack2(int v) {
     return (static_cast<unsigned>(v) & 0xFFFFu) * 0x00010001u;
 }
 
-// One column of one strip for both lanes.
+// One column of one strip for both lanes (kT query rows per strip).
 //   diag : (H - Goe)(r0 - 1, j - 1)       f : F(r0, j)
 // returns, through hm_out / f, (H - Goe)(r_last, j) and F(r_last + 1, j).
 // Per row r with S' = SM + Goe from the profile:
@@ -49,6 +46,7 @@ __device__ __forceinline__ unsigned pack2(int v) {
 //   E(r, j+1) = max(E(r, j) - Ge, Hm)                   Eq. sw3
 //   F(r+1, j) = max(F - Ge, H - Goe) = max(F - min(Ge, Goe), X - Goe)   Eq. sw4
 //   best   = max(best, X)     (max H = max X: every F is bounded by an earlier X or by 0)
+template <int kT>
 __device__ __forceinline__ void column(unsigned (&Hm)[kT], unsigned (&E)[kT], unsigned& f,
                                        unsigned& diag, const int16_t* qa, const int16_t* qb,
                                        const Packed& k, unsigned& best) {
@@ -86,6 +84,7 @@ __device__ __forceinline__ void column(unsigned (&Hm)[kT], unsigned (&E)[kT], un
 }
 
 // One strip (query rows [s*kT, s*kT + kT)) of one group: sweeps all L columns.
+template <int kT>
 __device__ __forceinline__ void strip(const uint4* __restrict__ res, int L, uint4* bnd,
                                       const int16_t* qp_strip, int qstride, bool first,
                                       bool last, const Packed& k, unsigned& best, int lane) {
@@ -139,7 +138,9 @@ __device__ __forceinline__ void emit(const InterParams& p, int q, int32_t* score
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_inter_i16x2(const InterParams p) {
+template <int kT, int kW, int kMinBlocks>
+__global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const InterParams p) {
+    constexpr int kBlock = kW * kWarp;
     extern __shared__ __align__(16) int16_t s_qp[];
     __shared__ int s_item;
     const int lane = threadIdx.x & (kWarp - 1);
@@ -182,8 +183,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_inter_i16x2(const InterParams p) 
             if (active && L > 0) {
                 const int s_end = min(S, (c0 + kQpRows) / kT);
                 for (int s = c0 / kT; s < s_end; ++s)
-                    strip(res, L, bnd, s_qp + (s * kT - c0), qstride, s == 0, s == S - 1, k,
-                          best, lane);
+                    strip<kT>(res, L, bnd, s_qp + (s * kT - c0), qstride, s == 0, s == S - 1,
+                              k, best, lane);
             }
         }
         if (active) {
@@ -196,31 +197,61 @@ __global__ void __launch_bounds__(kBlock, 4) k_inter_i16x2(const InterParams p) 
     }
 }
 
+// Variants: (rows per strip, warps per block).  Register budgets: 32 rows -> 121 registers
+// (4 blocks of 4 warps per SM); 64 rows -> <= 255 registers (2 blocks of 4 warps, or 1 of 8).
+struct InterVariant {
+    int T, W;
+    const void* fn;
+};
+
+template <int T, int W, int MB>
+void launch_variant(const InterParams& p, int grid, size_t smem, cudaStream_t st) {
+    k_inter_i16x2<T, W, MB><<<grid, W * kWarp, smem, st>>>(p);
+}
+
+const InterVariant kVariants[] = {
+    {32, 4, reinterpret_cast<const void*>(&k_inter_i16x2<32, 4, 4>)},
+    {64, 4, reinterpret_cast<const void*>(&k_inter_i16x2<64, 4, 2>)},
+    {32, 8, reinterpret_cast<const void*>(&k_inter_i16x2<32, 8, 2>)},
+    {64, 8, reinterpret_cast<const void*>(&k_inter_i16x2<64, 8, 1>)},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
 }  // namespace
 
-int inter_block_threads() { return kBlock; }
+int inter_num_variants() { return kNumVariants; }
+int inter_variant_rows(int v) { return kVariants[v].T; }
+int inter_variant_warps(int v) { return kVariants[v].W; }
 
 size_t inter_smem_bytes(int alphabet1) {
     return static_cast<size_t>(alphabet1) * (kQpRows + kQpPad) * sizeof(int16_t);
 }
 
-int inter_occupancy(int alphabet1) {
+int inter_occupancy(int variant, int alphabet1) {
+    if (variant < 0 || variant >= kNumVariants) return 0;
     int n = 0;
     const size_t smem = inter_smem_bytes(alphabet1);
-    cudaFuncSetAttribute(k_inter_i16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_inter_i16x2, kBlock, smem) !=
+    const void* fn = kVariants[variant].fn;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kVariants[variant].W * kWarp, smem) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
-cudaError_t launch_inter(const InterParams& p, int grid, int block, cudaStream_t st) {
+cudaError_t launch_inter(const InterParams& p, int variant, int grid, cudaStream_t st) {
+    if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
     const size_t smem = inter_smem_bytes(p.alphabet1);
-    cudaError_t e = cudaFuncSetAttribute(k_inter_i16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kVariants[variant].fn,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    k_inter_i16x2<<<grid, block, smem, st>>>(p);
+    switch (variant) {
+        case 0: launch_variant<32, 4, 4>(p, grid, smem, st); break;
+        case 1: launch_variant<64, 4, 2>(p, grid, smem, st); break;
+        case 2: launch_variant<32, 8, 2>(p, grid, smem, st); break;
+        default: launch_variant<64, 8, 1>(p, grid, smem, st); break;
+    }
     return cudaGetLastError();
 }
 

@@ -153,7 +153,7 @@ extern "C" sw_status sw_search_noalloc(const sw_db* db, const uint8_t* d_query, 
     if (static_cast<double>(std::min<int64_t>(query_len, v.max_len)) * max_s > 2147483647.0)
         return arg_error("scores could exceed the int32 range");
 
-    const int W = inter_block_threads() / kWarp;
+    const int W = inter_variant_warps(0);
     const int IW = intra_block_threads() / kWarp;
     const int64_t nchunks = (v.num_groups + W - 1) / W;
     if (nchunks > kMaxItems) return arg_error("database has more groups than the fixed work list holds");
@@ -239,7 +239,7 @@ extern "C" sw_status sw_search_noalloc(const sw_db* db, const uint8_t* d_query, 
         p.bnd = bnd;
         p.bnd_stride = bnd_stride;
         p.gaps = gaps;
-        NA_CU(launch_inter(p, static_cast<int>(inter_blocks), inter_block_threads(), st));
+        NA_CU(launch_inter(p, 0, static_cast<int>(inter_blocks), st));
         ++launches;
     }
     IntraParams ip{};

@@ -1,10 +1,12 @@
 // Host runtime of libswgb: the device-resident database, the search orchestration (query
 // profiles, persistent inter-task launch, intra-task launch for long subjects, int32 rescore
-// of saturated lanes, CUDA-graph replay) and the C ABI declared in include/swgb.h.
+// of saturated lanes), cached launch plans replayed as CUDA graphs, and the C ABI declared in
+// include/swgb.h.
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -16,6 +18,7 @@
 #include "../../include/swgb.h"
 #include "db_view.h"
 #include "layout.h"
+#include "runtime_internal.h"
 #include "swgb_device.cuh"
 
 using namespace swgb;
@@ -40,113 +43,262 @@ sw_status cuda_fail(cudaError_t e, const char* what) {
     return fail(st, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CU(call)                                                      \
-    do {                                                              \
-        cudaError_t e_ = (call);                                      \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
+#define CU(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-template <class T>
-struct DevBuf {
-    T* ptr = nullptr;
-    size_t cap = 0;   // elements
-    cudaError_t ensure(size_t n) {
-        if (n <= cap && ptr) return cudaSuccess;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        cap = 0;
-        const size_t want = std::max<size_t>(n, 1);
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), want * sizeof(T));
-        if (e == cudaSuccess) cap = want;
-        return e;
-    }
-    void release() {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        cap = 0;
-    }
-};
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-}  // namespace
-
-// A captured launch sequence, replayed when shapes and pointers repeat.
-struct GraphEntry {
-    std::vector<int64_t> key;
-    cudaGraphExec_t exec = nullptr;
-};
-
-struct sw_db {
-    int device = 0;
-    int sms = 0;
-    int32_t A = 0;
-    int32_t long_cutoff = 0;
-    int32_t flag_cap = 1 << 20;
-    Layout layout;
-    int64_t num_residues = 0;
-    // device database
-    DevBuf<uint8_t> inter;
-    DevBuf<int64_t> group_off;
-    DevBuf<int32_t> group_len;
-    DevBuf<int32_t> perm;
-    DevBuf<uint8_t> plain;
-    DevBuf<int64_t> plain_off;
-    DevBuf<int32_t> long_ids;
-    // workspace
-    DevBuf<int16_t> qp;
-    DevBuf<QueryDesc> descs;
-    DevBuf<InterItem> items;
-    DevBuf<int64_t> qp_off;
-    DevBuf<int32_t> mpad;
-    DevBuf<int64_t> qoff;
-    DevBuf<int32_t> query_order;
-    DevBuf<int8_t> matrix;
-    DevBuf<Control> ctrl;
-    DevBuf<FlagEntry> flags;
-    DevBuf<uint4> bnd;
-    DevBuf<int2> spill;
-    DevBuf<uint8_t> h_queries;   // device copy of host queries (host-buffer API)
-    DevBuf<int32_t> h_scores;    // device scores (host-buffer API)
-    cudaStream_t stream = nullptr;   // internal stream for the host-buffer API
-    cudaEvent_t ev[5] = {};
-    std::vector<GraphEntry> graphs;
-    // last search
-    sw_stats stats{};
-    bool stats_pending = false;
-    std::mutex mu;
-    int inter_occ = 0, intra_occ = 0;
-};
-
-namespace {
-
-void destroy_graphs(sw_db* db) {
-    for (auto& g : db->graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-    db->graphs.clear();
+bool graphs_enabled() {
+    const char* v = std::getenv("SWGB_GRAPHS");
+    return !(v && v[0] == '0');
 }
 
-sw_status validate_matrix(const int8_t* matrix, int32_t A, int* max_s) {
-    if (!matrix) return fail(SW_ERR_ARG, "matrix is null");
-    int mx = 0;
-    for (int i = 0; i < A * A; ++i) mx = std::max<int>(mx, matrix[i]);
-    *max_s = mx;
+}  // namespace
+
+namespace swgb {
+
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+}
+
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+sw_status set_last_error(sw_status st, const char* msg) { return fail(st, "%s", msg); }
+void add_launches(int64_t n) { g_launches += n; }
+
+void destroy_plans(sw_db* db) {
+    for (auto& p : db->plans) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    db->plans.clear();
+}
+
+// Grows the shared scratch (control block, saturation list, boundary buffers).  Cached plans
+// bake these pointers into their graphs, so a reallocation drops them.
+sw_status ensure_scratch(sw_db* db, size_t flag_cap, size_t bnd_elems, size_t spill_elems) {
+    const bool grow = !db->ctrl.ptr || flag_cap > db->flags.cap || bnd_elems > db->bnd.cap ||
+                      spill_elems > db->spill.cap;
+    if (!grow) return SW_OK;
+    if (db->stream) cudaStreamSynchronize(db->stream);
+    if (db->done_recorded) cudaEventSynchronize(db->ev[4]);
+    destroy_plans(db);
+    CU(db->ctrl.ensure(1));
+    CU(db->flags.ensure(std::max(flag_cap, db->flags.cap)));
+    CU(db->bnd.ensure(std::max(bnd_elems, db->bnd.cap)));
+    CU(db->spill.ensure(std::max(spill_elems, db->spill.cap)));
     return SW_OK;
 }
 
-// The whole search on device-resident queries.  `h_qoff` is host memory.
+// Builds the launch plan of one search shape: host tables, device copies, kernel parameters.
+sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t* h_matrix,
+                     int max_s, int32_t goe, int32_t ge, int32_t* d_scores,
+                     std::vector<int64_t> key, Plan** out) {
+    const int32_t A = db->A;
+    const int64_t N = db->layout.num_seqs;
+    auto plan = std::make_unique<Plan>();
+    Plan& P = *plan;
+    P.key = std::move(key);
+    P.nq = nq;
+    P.d_scores = d_scores;
+    P.int16_ok = goe <= 16383 && ge <= 16383;
+    P.qp_bias = (goe + 128 <= 32767) ? goe : 0;   // profile entries stay in int16
+    P.variant = db->variant;
+    P.m.resize(static_cast<size_t>(nq));
+    for (int q = 0; q < nq; ++q)
+        P.m[static_cast<size_t>(q)] = static_cast<int32_t>(h_qoff[q + 1] - h_qoff[q]);
+
+    std::vector<int64_t> qp_off(static_cast<size_t>(nq));
+    std::vector<int32_t> mpad(static_cast<size_t>(nq));
+    int64_t total_qp = 0;
+    for (int q = 0; q < nq; ++q) {
+        const int64_t mp = round_up(std::max<int64_t>(P.m[static_cast<size_t>(q)], 1), kQpRows);
+        mpad[static_cast<size_t>(q)] = static_cast<int32_t>(mp);
+        qp_off[static_cast<size_t>(q)] = total_qp;
+        total_qp += mp * (A + 1);
+        P.max_mpad = std::max(P.max_mpad, mp);
+    }
+    std::vector<int32_t> order(static_cast<size_t>(nq));
+    for (int q = 0; q < nq; ++q) order[static_cast<size_t>(q)] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return P.m[static_cast<size_t>(a)] > P.m[static_cast<size_t>(b)];
+    });
+
+    // Work items of the inter-task kernel: (query, W consecutive groups), largest first.
+    const int W = inter_variant_warps(P.variant);
+    std::vector<InterItem> items;
+    const int64_t G = db->layout.num_groups;
+    if (P.int16_ok && G > 0) {
+        const int64_t chunks = (G + W - 1) / W;
+        std::vector<int64_t> cost;
+        items.reserve(static_cast<size_t>(chunks * nq));
+        cost.reserve(static_cast<size_t>(chunks * nq));
+        for (int32_t q : order) {
+            if (P.m[static_cast<size_t>(q)] == 0) continue;
+            for (int64_t c = chunks - 1; c >= 0; --c) {
+                const int64_t g0 = c * W;
+                const int32_t ng = static_cast<int32_t>(std::min<int64_t>(W, G - g0));
+                items.push_back(InterItem{q, static_cast<int32_t>(g0), ng, 0});
+                cost.push_back(static_cast<int64_t>(P.m[static_cast<size_t>(q)]) *
+                               db->layout.group_len[static_cast<size_t>(g0 + ng - 1)]);
+            }
+        }
+        std::vector<int32_t> idx(items.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = static_cast<int32_t>(i);
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+        std::vector<InterItem> sorted(items.size());
+        for (size_t i = 0; i < idx.size(); ++i) sorted[i] = items[static_cast<size_t>(idx[i])];
+        items.swap(sorted);
+    }
+    P.num_items = static_cast<int64_t>(items.size());
+    if (P.num_items > INT32_MAX) return fail(SW_ERR_ARG, "too many work items");
+
+    // Scratch shared by all plans of this database.
+    P.inter_grid = db->sms * std::max(1, db->inter_occ[P.variant]);
+    P.intra_grid = db->sms * std::max(1, db->intra_occ);
+    const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
+    const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
+    const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
+    const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
+    P.flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));
+    sw_status s = ensure_scratch(db, P.flag_cap, static_cast<size_t>(inter_slots * bnd_stride),
+                                 static_cast<size_t>(intra_slots * spill_stride));
+    if (s != SW_OK) return s;
+
+    // Plan-owned device tables (uploaded once, synchronously, on the database's own stream).
+    CU(P.qp.ensure(static_cast<size_t>(total_qp)));
+    CU(P.descs.ensure(static_cast<size_t>(nq)));
+    CU(P.items.ensure(std::max<size_t>(items.size(), 1)));
+    CU(P.qp_off.ensure(static_cast<size_t>(nq)));
+    CU(P.mpad.ensure(static_cast<size_t>(nq)));
+    CU(P.qoff.ensure(static_cast<size_t>(nq) + 1));
+    CU(P.order.ensure(static_cast<size_t>(nq)));
+    CU(P.matrix.ensure(static_cast<size_t>(A * A)));
+    std::vector<QueryDesc> descs(static_cast<size_t>(nq));
+    for (int q = 0; q < nq; ++q)
+        descs[static_cast<size_t>(q)] = QueryDesc{P.qp.ptr + qp_off[static_cast<size_t>(q)],
+                                                  d_scores + static_cast<int64_t>(q) * N,
+                                                  P.m[static_cast<size_t>(q)], mpad[static_cast<size_t>(q)]};
+    cudaStream_t us = db->stream;
+    CU(cudaMemcpyAsync(P.descs.ptr, descs.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, us));
+    if (!items.empty())
+        CU(cudaMemcpyAsync(P.items.ptr, items.data(), sizeof(InterItem) * items.size(),
+                           cudaMemcpyHostToDevice, us));
+    CU(cudaMemcpyAsync(P.qp_off.ptr, qp_off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, us));
+    CU(cudaMemcpyAsync(P.mpad.ptr, mpad.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, us));
+    CU(cudaMemcpyAsync(P.qoff.ptr, h_qoff, sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, us));
+    CU(cudaMemcpyAsync(P.order.ptr, order.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, us));
+    CU(cudaMemcpyAsync(P.matrix.ptr, h_matrix, static_cast<size_t>(A * A), cudaMemcpyHostToDevice, us));
+    CU(cudaStreamSynchronize(us));
+
+    const Gaps gaps{goe, ge, std::min(goe, ge)};
+    InterParams& ip = P.inter;
+    ip.inter = db->inter.ptr;
+    ip.group_off = db->group_off.ptr;
+    ip.group_len = db->group_len.ptr;
+    ip.perm = db->perm.ptr;
+    ip.queries = P.descs.ptr;
+    ip.items = P.items.ptr;
+    ip.num_items = static_cast<int32_t>(P.num_items);
+    ip.alphabet1 = A + 1;
+    ip.ctrl = db->ctrl.ptr;
+    ip.flags = db->flags.ptr;
+    ip.flag_cap = P.flag_cap;
+    ip.thresh = 32767 - std::max(0, max_s);
+    ip.bnd = db->bnd.ptr;
+    ip.bnd_stride = bnd_stride;
+    ip.gaps = gaps;
+    IntraParams& jp = P.intra;
+    jp.plain = db->plain.ptr;
+    jp.plain_off = db->plain_off.ptr;
+    jp.queries = P.descs.ptr;
+    jp.num_queries = nq;
+    jp.long_ids = db->long_ids.ptr;
+    jp.num_long = static_cast<int64_t>(db->layout.long_ids.size());
+    jp.query_order = P.order.ptr;
+    jp.num_seqs = N;
+    jp.flags = db->flags.ptr;
+    jp.flag_cap = P.flag_cap;
+    jp.alphabet1 = A + 1;
+    jp.ctrl = db->ctrl.ptr;
+    jp.spill = db->spill.ptr;
+    jp.spill_stride = spill_stride;
+    jp.gaps = gaps;
+    jp.qp_add = goe - P.qp_bias;
+
+    for (int q = 0; q < nq; ++q) {
+        P.cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * db->num_residues;
+        if (P.int16_ok)
+            P.inter_cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * db->layout.short_residues;
+    }
+    if (db->plans.size() >= 8) {
+        if (db->done_recorded) cudaEventSynchronize(db->ev[4]);   // its graph may still run
+        if (db->plans.front()->exec) cudaGraphExecDestroy(db->plans.front()->exec);
+        db->plans.erase(db->plans.begin());
+    }
+    db->plans.push_back(std::move(plan));
+    *out = db->plans.back().get();
+    return SW_OK;
+}
+
+// Event records become external event nodes when captured, so the timing events (and ev[4],
+// which orders the next search) stay usable after a graph replay.
+cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+               : cudaEventRecord(ev, st);
+}
+
+// Enqueues the launch sequence of a plan on `st` (captured into a graph or run directly).
+sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_t st) {
+    const int64_t N = db->layout.num_seqs;
+    int64_t launches = 0;
+    CU(record(db->ev[0], st));
+    CU(cudaMemsetAsync(db->ctrl.ptr, 0, sizeof(Control), st));
+    for (int q = 0; q < P.nq; ++q)   // empty queries score 0 everywhere
+        if (P.m[static_cast<size_t>(q)] == 0 && N > 0)
+            CU(cudaMemsetAsync(P.d_scores + static_cast<int64_t>(q) * N, 0, sizeof(int32_t) * N, st));
+    CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
+                       P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
+    ++launches;
+    CU(record(db->ev[1], st));
+    if (P.num_items > 0) {
+        CU(launch_inter(P.inter, P.variant, P.inter_grid, st));
+        ++launches;
+    }
+    CU(record(db->ev[2], st));
+    IntraParams jp = P.intra;
+    if (!P.int16_ok) {
+        jp.mode = kIntraAll;
+        if (N > 0) {
+            CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            ++launches;
+        }
+    } else if (jp.num_long > 0) {
+        jp.mode = kIntraLong;
+        CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+        ++launches;
+    }
+    CU(record(db->ev[3], st));
+    if (P.int16_ok && P.num_items > 0) {
+        jp.mode = kIntraRescore;
+        CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+        ++launches;
+    }
+    CU(record(db->ev[4], st));
+    P.launches = launches;
+    return SW_OK;
+}
+
 sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qoff, int32_t nq,
                         const int8_t* h_matrix, int32_t gap_open, int32_t gap_extend,
                         int32_t* d_scores, cudaStream_t st) {
@@ -156,190 +308,81 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     if (nq == 0) return SW_OK;
     if (!h_qoff || !d_scores || (!d_queries && h_qoff[nq] > 0))
         return fail(SW_ERR_ARG, "null query/offset/score pointer");
+    if (!h_matrix) return fail(SW_ERR_ARG, "matrix is null");
     const int32_t A = db->A;
     int max_s = 0;
-    sw_status vs = validate_matrix(h_matrix, A, &max_s);
-    if (vs != SW_OK) return vs;
+    for (int i = 0; i < A * A; ++i) max_s = std::max<int>(max_s, h_matrix[i]);
     if (h_qoff[0] != 0) return fail(SW_ERR_ARG, "query_offsets[0] must be 0");
-    std::vector<int32_t> m(static_cast<size_t>(nq));
     int64_t max_m = 0;
     for (int q = 0; q < nq; ++q) {
         const int64_t len = h_qoff[q + 1] - h_qoff[q];
         if (len < 0 || len > (int64_t{1} << 28))
             return fail(SW_ERR_ARG, "query %d: bad length %lld", q, static_cast<long long>(len));
-        m[static_cast<size_t>(q)] = static_cast<int32_t>(len);
         max_m = std::max(max_m, len);
     }
     if (static_cast<double>(std::min<int64_t>(max_m, db->layout.max_len)) * max_s > 2147483647.0)
         return fail(SW_ERR_ARG, "scores could exceed the int32 range");
-    const int64_t N = db->layout.num_seqs;
-    const int32_t goe = gap_open, ge = gap_extend, gep = std::min(goe, ge);
-    const bool int16_ok = goe <= 16383 && ge <= 16383;
-    const int32_t qp_bias = (goe + 128 <= 32767) ? goe : 0;   // profile entries stay in int16
+    if (db->layout.num_seqs == 0) return SW_OK;
 
-    // ---- plan: profiles, descriptors, items
-    std::vector<int64_t> qp_off(static_cast<size_t>(nq));
-    std::vector<int32_t> mpad(static_cast<size_t>(nq));
-    int64_t total_qp = 0, max_mpad = 0;
-    for (int q = 0; q < nq; ++q) {
-        const int64_t mp = round_up(std::max<int64_t>(m[static_cast<size_t>(q)], 1), kQpRows);
-        mpad[static_cast<size_t>(q)] = static_cast<int32_t>(mp);
-        qp_off[static_cast<size_t>(q)] = total_qp;
-        total_qp += mp * (A + 1);
-        max_mpad = std::max(max_mpad, mp);
+    // Identity of this search shape: pointers, lengths, costs, matrix, kernel variant.
+    std::vector<int64_t> key;
+    key.reserve(static_cast<size_t>(nq) + 8 + static_cast<size_t>(A * A));
+    key.push_back(reinterpret_cast<int64_t>(d_queries));
+    key.push_back(reinterpret_cast<int64_t>(d_scores));
+    key.push_back(nq);
+    key.push_back(gap_open);
+    key.push_back(gap_extend);
+    key.push_back(db->variant);
+    for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
+    for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
+
+    Plan* plan = nullptr;
+    for (auto& p : db->plans)
+        if (p->key == key) plan = p.get();
+    if (!plan) {
+        sw_status s = build_plan(db, h_qoff, nq, h_matrix, max_s, gap_open, gap_extend, d_scores,
+                                 key, &plan);
+        if (s != SW_OK) return s;
     }
-    std::vector<int32_t> order(static_cast<size_t>(nq));
-    for (int q = 0; q < nq; ++q) order[static_cast<size_t>(q)] = q;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return m[static_cast<size_t>(a)] > m[static_cast<size_t>(b)]; });
-
-    const int W = inter_block_threads() / kWarp;
-    std::vector<InterItem> items;
-    const int64_t G = db->layout.num_groups;
-    if (int16_ok && G > 0) {
-        const int64_t chunks = (G + W - 1) / W;
-        items.reserve(static_cast<size_t>(chunks * nq));
-        // queries longest first, groups longest first: big items start early, the tail is short
-        for (int32_t q : order) {
-            if (m[static_cast<size_t>(q)] == 0) continue;
-            for (int64_t c = chunks - 1; c >= 0; --c) {
-                const int64_t g0 = c * W;
-                const int32_t ng = static_cast<int32_t>(std::min<int64_t>(W, G - g0));
-                items.push_back(InterItem{q, static_cast<int32_t>(g0), ng, 0});
+    // Searches on one database share scratch: order this one after the previous one,
+    // whatever stream that ran on.
+    if (db->done_recorded) CU(cudaStreamWaitEvent(st, db->ev[4], 0));
+    bool replay = false;
+    if (graphs_enabled()) {
+        if (!plan->exec) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(db->capture_stream, cudaStreamCaptureModeThreadLocal));
+            sw_status s = enqueue_plan(db, *plan, d_queries, db->capture_stream);
+            cudaError_t ec = cudaStreamEndCapture(db->capture_stream, &graph);
+            if (s != SW_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
             }
+            if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+            ec = cudaGraphInstantiate(&plan->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) {
+                plan->exec = nullptr;
+                return cuda_fail(ec, "cudaGraphInstantiate");
+            }
+        } else {
+            replay = true;
         }
-        std::vector<int64_t> cost(items.size());
-        for (size_t i = 0; i < items.size(); ++i) {
-            const InterItem& it = items[i];
-            const int64_t L = db->layout.group_len[static_cast<size_t>(it.group + it.ngroups - 1)];
-            cost[i] = static_cast<int64_t>(m[static_cast<size_t>(it.query)]) * L;
-        }
-        std::vector<int32_t> idx(items.size());
-        for (size_t i = 0; i < idx.size(); ++i) idx[i] = static_cast<int32_t>(i);
-        std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-        std::vector<InterItem> sorted(items.size());
-        for (size_t i = 0; i < idx.size(); ++i) sorted[i] = items[static_cast<size_t>(idx[i])];
-        items.swap(sorted);
+        CU(cudaGraphLaunch(plan->exec, st));
+    } else {
+        sw_status s = enqueue_plan(db, *plan, d_queries, st);
+        if (s != SW_OK) return s;
     }
-
-    // ---- workspace
-    const int inter_grid = db->sms * std::max(1, db->inter_occ);
-    const int intra_grid = db->sms * std::max(1, db->intra_occ);
-    const int64_t inter_slots = static_cast<int64_t>(inter_grid) * W;
-    const int64_t intra_slots = static_cast<int64_t>(intra_grid) * (intra_block_threads() / kWarp);
-    const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
-    const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
-    const uint32_t flag_cap =
-        static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));
-    CU(db->qp.ensure(static_cast<size_t>(total_qp)));
-    CU(db->descs.ensure(static_cast<size_t>(nq)));
-    CU(db->items.ensure(std::max<size_t>(items.size(), 1)));
-    CU(db->qp_off.ensure(static_cast<size_t>(nq)));
-    CU(db->mpad.ensure(static_cast<size_t>(nq)));
-    CU(db->qoff.ensure(static_cast<size_t>(nq) + 1));
-    CU(db->query_order.ensure(static_cast<size_t>(nq)));
-    CU(db->matrix.ensure(static_cast<size_t>(A * A)));
-    CU(db->ctrl.ensure(1));
-    CU(db->flags.ensure(flag_cap));
-    if (!items.empty()) CU(db->bnd.ensure(static_cast<size_t>(inter_slots * bnd_stride)));
-    CU(db->spill.ensure(static_cast<size_t>(intra_slots * spill_stride)));
-
-    std::vector<QueryDesc> descs(static_cast<size_t>(nq));
-    for (int q = 0; q < nq; ++q)
-        descs[static_cast<size_t>(q)] = QueryDesc{db->qp.ptr + qp_off[static_cast<size_t>(q)],
-                                                  d_scores + static_cast<int64_t>(q) * N,
-                                                  m[static_cast<size_t>(q)], mpad[static_cast<size_t>(q)]};
-    CU(cudaMemcpyAsync(db->descs.ptr, descs.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, st));
-    if (!items.empty())
-        CU(cudaMemcpyAsync(db->items.ptr, items.data(), sizeof(InterItem) * items.size(),
-                           cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(db->qp_off.ptr, qp_off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(db->mpad.ptr, mpad.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(db->qoff.ptr, h_qoff, sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(db->query_order.ptr, order.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(db->matrix.ptr, h_matrix, static_cast<size_t>(A * A), cudaMemcpyHostToDevice, st));
-
-    // ---- launch sequence
-    int64_t launches = 0;
-    CU(cudaEventRecord(db->ev[0], st));
-    CU(cudaMemsetAsync(db->ctrl.ptr, 0, sizeof(Control), st));
-    for (int q = 0; q < nq; ++q)   // empty queries score 0 everywhere
-        if (m[static_cast<size_t>(q)] == 0 && N > 0)
-            CU(cudaMemsetAsync(d_scores + static_cast<int64_t>(q) * N, 0, sizeof(int32_t) * N, st));
-    CU(launch_build_qp(d_queries, db->qoff.ptr, nq, db->matrix.ptr, A, qp_bias, db->qp_off.ptr,
-                       db->mpad.ptr, db->qp.ptr, max_mpad, db->ctrl.ptr, st));
-    ++launches;
-    CU(cudaEventRecord(db->ev[1], st));
-    const Gaps gaps{goe, ge, gep};
-    if (!items.empty()) {
-        InterParams p{};
-        p.inter = db->inter.ptr;
-        p.group_off = db->group_off.ptr;
-        p.group_len = db->group_len.ptr;
-        p.perm = db->perm.ptr;
-        p.queries = db->descs.ptr;
-        p.items = db->items.ptr;
-        p.num_items = static_cast<int32_t>(items.size());
-        p.alphabet1 = A + 1;
-        p.ctrl = db->ctrl.ptr;
-        p.flags = db->flags.ptr;
-        p.flag_cap = flag_cap;
-        p.thresh = 32767 - std::max(0, max_s);
-        p.bnd = db->bnd.ptr;
-        p.bnd_stride = bnd_stride;
-        p.gaps = gaps;
-        CU(launch_inter(p, inter_grid, inter_block_threads(), st));
-        ++launches;
-    }
-    CU(cudaEventRecord(db->ev[2], st));
-    IntraParams ip{};
-    ip.plain = db->plain.ptr;
-    ip.plain_off = db->plain_off.ptr;
-    ip.queries = db->descs.ptr;
-    ip.num_queries = nq;
-    ip.long_ids = db->long_ids.ptr;
-    ip.num_long = static_cast<int64_t>(db->layout.long_ids.size());
-    ip.query_order = db->query_order.ptr;
-    ip.num_seqs = N;
-    ip.flags = db->flags.ptr;
-    ip.flag_cap = flag_cap;
-    ip.alphabet1 = A + 1;
-    ip.ctrl = db->ctrl.ptr;
-    ip.spill = db->spill.ptr;
-    ip.spill_stride = spill_stride;
-    ip.gaps = gaps;
-    ip.qp_add = goe - qp_bias;
-    if (!int16_ok) {
-        ip.mode = kIntraAll;
-        if (N > 0) {
-            CU(launch_intra(ip, intra_grid, intra_block_threads(), st));
-            ++launches;
-        }
-    } else if (ip.num_long > 0) {
-        ip.mode = kIntraLong;
-        CU(launch_intra(ip, intra_grid, intra_block_threads(), st));
-        ++launches;
-    }
-    CU(cudaEventRecord(db->ev[3], st));
-    if (int16_ok && !items.empty()) {
-        ip.mode = kIntraRescore;
-        CU(launch_intra(ip, intra_grid, intra_block_threads(), st));
-        ++launches;
-    }
-    CU(cudaEventRecord(db->ev[4], st));
-    g_launches += launches;
-
-    int64_t cells = 0, inter_cells = 0;
-    for (int q = 0; q < nq; ++q) {
-        cells += static_cast<int64_t>(m[static_cast<size_t>(q)]) * db->num_residues;
-        if (int16_ok) inter_cells += static_cast<int64_t>(m[static_cast<size_t>(q)]) * db->layout.short_residues;
-    }
+    db->done_recorded = true;
+    g_launches += plan->launches;
     db->stats = sw_stats{};
-    db->stats.cells = cells;
-    db->stats.inter_cells = inter_cells;
-    db->stats.launches = launches;
-    db->stats.inter_grid = inter_grid;
-    db->stats.inter_block = inter_block_threads();
+    db->stats.cells = plan->cells;
+    db->stats.inter_cells = plan->inter_cells;
+    db->stats.launches = plan->launches;
+    db->stats.inter_grid = plan->inter_grid;
+    db->stats.inter_block = inter_variant_warps(plan->variant) * kWarp;
+    db->stats.graph_replay = replay ? 1 : 0;
+    db->stats.variant = plan->variant;
     db->stats_pending = true;
     return SW_OK;
 }
@@ -364,14 +407,39 @@ sw_status finish_stats(sw_db* db) {
     return SW_OK;
 }
 
-}  // namespace
+bool db_view(const sw_db* db, DbView* v) {
+    if (!db || !v) return false;
+    v->device = db->device;
+    v->sms = db->sms;
+    v->alphabet = db->A;
+    v->num_seqs = db->layout.num_seqs;
+    v->num_residues = db->num_residues;
+    v->short_residues = db->layout.short_residues;
+    v->num_groups = db->layout.num_groups;
+    v->max_group_len = db->layout.max_group_len;
+    v->max_len = db->layout.max_len;
+    v->num_long = static_cast<int64_t>(db->layout.long_ids.size());
+    v->flag_cap = db->flag_cap;
+    v->inter_occ = db->inter_occ[0];
+    v->intra_occ = db->intra_occ;
+    v->inter = db->inter.ptr;
+    v->group_off = db->group_off.ptr;
+    v->group_len = db->group_len.ptr;
+    v->perm = db->perm.ptr;
+    v->plain = db->plain.ptr;
+    v->plain_off = db->plain_off.ptr;
+    v->long_ids = db->long_ids.ptr;
+    return true;
+}
+
+}  // namespace swgb
 
 // ================================================================= C ABI
 
 extern "C" {
 
 const char* sw_last_error(void) { return g_err.c_str(); }
-const char* sw_version(void) { return "swgb 0.1 (sm_103a)"; }
+const char* sw_version(void) { return "swgb 0.2 (sm_103a)"; }
 int64_t sw_launch_count(void) { return g_launches.load(); }
 
 sw_status sw_layout_sizes(const int64_t* offsets, int64_t num_seqs, int32_t long_cutoff,
@@ -439,11 +507,18 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     db->num_residues = R;
     DeviceGuard guard(dev);
     CU(cudaDeviceGetAttribute(&db->sms, cudaDevAttrMultiProcessorCount, dev));
-    db->inter_occ = inter_occupancy(alphabet_size + 1);
+    for (int v = 0; v < inter_num_variants() && v < kMaxVariants; ++v)
+        db->inter_occ[v] = inter_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
-    if (db->inter_occ <= 0 || db->intra_occ <= 0)
+    if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
+    const char* forced = std::getenv("SWGB_VARIANT");
+    if (forced) {
+        const int v = std::atoi(forced);
+        if (v >= 0 && v < inter_num_variants() && db->inter_occ[v] > 0) db->variant = v;
+    }
     CU(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&db->capture_stream, cudaStreamNonBlocking));
     for (auto& e : db->ev) CU(cudaEventCreate(&e));
     const Layout& L = db->layout;
     std::vector<uint8_t> inter(static_cast<size_t>(std::max<int64_t>(L.inter_bytes, 1)));
@@ -454,9 +529,12 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     CU(db->group_len.ensure(L.group_len.size()));
     CU(db->perm.ensure(L.perm.size()));
     if (!L.group_off.empty()) {
-        CU(cudaMemcpy(db->group_off.ptr, L.group_off.data(), sizeof(int64_t) * L.group_off.size(), cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(db->group_len.ptr, L.group_len.data(), sizeof(int32_t) * L.group_len.size(), cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(db->perm.ptr, L.perm.data(), sizeof(int32_t) * L.perm.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db->group_off.ptr, L.group_off.data(), sizeof(int64_t) * L.group_off.size(),
+                      cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db->group_len.ptr, L.group_len.data(), sizeof(int32_t) * L.group_len.size(),
+                      cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db->perm.ptr, L.perm.data(), sizeof(int32_t) * L.perm.size(),
+                      cudaMemcpyHostToDevice));
     }
     CU(db->plain.ensure(static_cast<size_t>(std::max<int64_t>(R, 16))));
     if (R > 0) CU(cudaMemcpy(db->plain.ptr, residues, static_cast<size_t>(R), cudaMemcpyHostToDevice));
@@ -464,7 +542,8 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     CU(cudaMemcpy(db->plain_off.ptr, offsets, sizeof(int64_t) * (num_seqs + 1), cudaMemcpyHostToDevice));
     CU(db->long_ids.ensure(std::max<size_t>(L.long_ids.size(), 1)));
     if (!L.long_ids.empty())
-        CU(cudaMemcpy(db->long_ids.ptr, L.long_ids.data(), sizeof(int32_t) * L.long_ids.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db->long_ids.ptr, L.long_ids.data(), sizeof(int32_t) * L.long_ids.size(),
+                      cudaMemcpyHostToDevice));
     *out = db.release();
     return SW_OK;
 }
@@ -479,22 +558,16 @@ void sw_db_free(sw_db* db) {
     {
         DeviceGuard guard(db->device);
         if (db->stream) cudaStreamSynchronize(db->stream);
-        destroy_graphs(db);
-        DevBuf<uint8_t>* u8s[] = {&db->inter, &db->plain, &db->h_queries};
-        for (auto* b : u8s) b->release();
+        if (db->done_recorded) cudaEventSynchronize(db->ev[4]);
+        destroy_plans(db);
+        db->inter.release();
+        db->plain.release();
+        db->h_queries.release();
         db->group_off.release();
         db->group_len.release();
         db->perm.release();
         db->plain_off.release();
         db->long_ids.release();
-        db->qp.release();
-        db->descs.release();
-        db->items.release();
-        db->qp_off.release();
-        db->mpad.release();
-        db->qoff.release();
-        db->query_order.release();
-        db->matrix.release();
         db->ctrl.release();
         db->flags.release();
         db->bnd.release();
@@ -503,6 +576,7 @@ void sw_db_free(sw_db* db) {
         for (auto& e : db->ev)
             if (e) cudaEventDestroy(e);
         if (db->stream) cudaStreamDestroy(db->stream);
+        if (db->capture_stream) cudaStreamDestroy(db->capture_stream);
     }
     delete db;
 }
@@ -522,9 +596,9 @@ sw_status sw_search_batch_device(const sw_db* cdb, const uint8_t* d_queries,
                          d_scores, static_cast<cudaStream_t>(stream));
 }
 
-sw_status sw_search_batch(const sw_db* cdb, const uint8_t* const* queries, const int32_t* query_lens,
-                          int32_t num_queries, const int8_t* matrix, int32_t gap_open,
-                          int32_t gap_extend, int32_t* scores) {
+sw_status sw_search_batch(const sw_db* cdb, const uint8_t* const* queries,
+                          const int32_t* query_lens, int32_t num_queries, const int8_t* matrix,
+                          int32_t gap_open, int32_t gap_extend, int32_t* scores) {
     if (!cdb) return fail(SW_ERR_ARG, "db is null");
     if (num_queries < 0) return fail(SW_ERR_ARG, "num_queries < 0");
     if (num_queries > 0 && (!queries || !query_lens || !scores))
@@ -540,14 +614,16 @@ sw_status sw_search_batch(const sw_db* cdb, const uint8_t* const* queries, const
         qoff[static_cast<size_t>(q) + 1] = qoff[static_cast<size_t>(q)] + query_lens[q];
     }
     std::vector<uint8_t> cat(static_cast<size_t>(std::max<int64_t>(qoff.back(), 1)));
-    for (int q = 0; q < num_queries; ++q) {
-        if (query_lens[q] > 0) std::memcpy(cat.data() + qoff[static_cast<size_t>(q)], queries[q], static_cast<size_t>(query_lens[q]));
-    }
+    for (int q = 0; q < num_queries; ++q)
+        if (query_lens[q] > 0)
+            std::memcpy(cat.data() + qoff[static_cast<size_t>(q)], queries[q],
+                        static_cast<size_t>(query_lens[q]));
     for (int64_t i = 0; i < qoff.back(); ++i)
         if (cat[static_cast<size_t>(i)] >= db->A)
             return fail(SW_ERR_CODE, "query residue %lld has code %d >= alphabet_size %d",
                         static_cast<long long>(i), cat[static_cast<size_t>(i)], db->A);
     if (num_queries == 0 || N == 0) return SW_OK;
+    if (db->done_recorded) CU(cudaEventSynchronize(db->ev[4]));   // staging buffers may move
     CU(db->h_queries.ensure(cat.size()));
     CU(db->h_scores.ensure(static_cast<size_t>(N * num_queries)));
     CU(cudaMemcpyAsync(db->h_queries.ptr, cat.data(), cat.size(), cudaMemcpyHostToDevice, db->stream));
@@ -579,39 +655,3 @@ sw_status sw_get_stats(const sw_db* cdb, sw_stats* out) {
 }
 
 }  // extern "C"
-
-// ================================================================= internal accessors
-// Read-only view of a loaded database for other translation units of the library.
-
-namespace swgb {
-
-bool db_view(const sw_db* db, DbView* v) {
-    if (!db || !v) return false;
-    v->device = db->device;
-    v->sms = db->sms;
-    v->alphabet = db->A;
-    v->num_seqs = db->layout.num_seqs;
-    v->num_residues = db->num_residues;
-    v->short_residues = db->layout.short_residues;
-    v->num_groups = db->layout.num_groups;
-    v->max_group_len = db->layout.max_group_len;
-    v->max_len = db->layout.max_len;
-    v->num_long = static_cast<int64_t>(db->layout.long_ids.size());
-    v->flag_cap = db->flag_cap;
-    v->inter_occ = db->inter_occ;
-    v->intra_occ = db->intra_occ;
-    v->inter = db->inter.ptr;
-    v->group_off = db->group_off.ptr;
-    v->group_len = db->group_len.ptr;
-    v->perm = db->perm.ptr;
-    v->plain = db->plain.ptr;
-    v->plain_off = db->plain_off.ptr;
-    v->long_ids = db->long_ids.ptr;
-    return true;
-}
-
-sw_status set_last_error(sw_status st, const char* msg) { return fail(st, "%s", msg); }
-
-void add_launches(int64_t n) { g_launches += n; }
-
-}  // namespace swgb

@@ -1,0 +1,119 @@
+// Internal state of a loaded database (sw_db) and of a cached launch plan.  Shared by the
+// runtime's translation units; not part of the C ABI.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/swgb.h"
+#include "layout.h"
+#include "swgb_device.cuh"
+
+namespace swgb {
+
+constexpr int kMaxVariants = 8;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+template <class T>
+struct DevBuf {
+    T* ptr = nullptr;
+    size_t cap = 0;   // elements
+    cudaError_t ensure(size_t n) {
+        if (n <= cap && ptr) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(n, 1);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), want * sizeof(T));
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Everything one search shape needs besides the shared scratch: its own profile buffer and
+// tables, the kernel parameters, and the instantiated CUDA graph of its launch sequence.
+struct Plan {
+    std::vector<int64_t> key;
+    int nq = 0;
+    std::vector<int32_t> m;
+    int32_t* d_scores = nullptr;
+    bool int16_ok = true;
+    int32_t qp_bias = 0;
+    int variant = 0;
+    int64_t max_mpad = 0;
+    int64_t num_items = 0;
+    int inter_grid = 0, intra_grid = 0;
+    uint32_t flag_cap = 0;
+    int64_t cells = 0, inter_cells = 0, launches = 0;
+    DevBuf<int16_t> qp;
+    DevBuf<QueryDesc> descs;
+    DevBuf<InterItem> items;
+    DevBuf<int64_t> qp_off;
+    DevBuf<int32_t> mpad;
+    DevBuf<int64_t> qoff;
+    DevBuf<int32_t> order;
+    DevBuf<int8_t> matrix;
+    InterParams inter{};
+    IntraParams intra{};
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace swgb
+
+struct sw_db {
+    int device = 0;
+    int sms = 0;
+    int32_t A = 0;
+    int32_t long_cutoff = 0;
+    int32_t flag_cap = 1 << 20;
+    swgb::Layout layout;
+    int64_t num_residues = 0;
+    // device database
+    swgb::DevBuf<uint8_t> inter;
+    swgb::DevBuf<int64_t> group_off;
+    swgb::DevBuf<int32_t> group_len;
+    swgb::DevBuf<int32_t> perm;
+    swgb::DevBuf<uint8_t> plain;
+    swgb::DevBuf<int64_t> plain_off;
+    swgb::DevBuf<int32_t> long_ids;
+    // scratch shared by all searches on this database (ordered on the device by ev[4])
+    swgb::DevBuf<swgb::Control> ctrl;
+    swgb::DevBuf<swgb::FlagEntry> flags;
+    swgb::DevBuf<uint4> bnd;
+    swgb::DevBuf<int2> spill;
+    // host-buffer API staging
+    swgb::DevBuf<uint8_t> h_queries;
+    swgb::DevBuf<int32_t> h_scores;
+    cudaStream_t stream = nullptr;           // stream of the host-buffer API
+    cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
+    cudaEvent_t ev[5] = {};                  // per-kernel timing; ev[4] = end of the last search
+    bool done_recorded = false;
+    std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 8
+    // kernel choice
+    int variant = 0;
+    int inter_occ[swgb::kMaxVariants] = {};
+    int intra_occ = 0;
+    // last search
+    sw_stats stats{};
+    bool stats_pending = false;
+    std::mutex mu;
+};

@@ -110,10 +110,13 @@ cudaError_t launch_build_qp(const uint8_t* d_queries, const int64_t* d_qoff, int
                             const int8_t* d_matrix, int32_t A, int32_t bias,
                             const int64_t* d_qp_off, const int32_t* d_mpad, int16_t* d_qp,
                             int64_t max_mpad, Control* ctrl, cudaStream_t st);
-cudaError_t launch_inter(const InterParams& p, int grid, int block, cudaStream_t st);
-int inter_block_threads();
+// Inter-task kernel variants (rows per strip x warps per block), chosen by the autotuner.
+int inter_num_variants();
+int inter_variant_rows(int variant);
+int inter_variant_warps(int variant);
 size_t inter_smem_bytes(int alphabet1);
-int inter_occupancy(int alphabet1);
+int inter_occupancy(int variant, int alphabet1);
+cudaError_t launch_inter(const InterParams& p, int variant, int grid, cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
 int intra_block_threads();
 int intra_rows_per_pass();

@@ -212,3 +212,47 @@ def test_results_independent_of_routing(sw):
         with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE, long_cutoff=cutoff) as h:
             outs.append(sw.sw_search(h, wl.queries[0], wl.matrix, 10, 2))
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_every_kernel_variant_and_autotuner(sw, tmp_path):
+    """Each inter-task variant (rows per strip x warps per block) gives the oracle's scores;
+    the autotuner picks one, stores it in the cache and reuses it from there."""
+    wl = w.batched(seed=12, scale=0.004, query_lengths=[100, 333, 700])
+    exp = _oracle_all(wl.queries, wl.db, wl.matrix, 10, 2)
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        for v in range(4):
+            sw.sw_db_set_variant(h, v)
+            got = sw.sw_search_batch(h, wl.queries, wl.matrix, 10, 2)
+            assert sw.sw_get_stats(h)["variant"] == v
+            _check(got, exp, f"variant {v}")
+        cache = str(tmp_path / "tune.txt")
+        r1 = sw.sw_db_tune(h, [wl.queries[1]], wl.matrix, 10, 2, cache_path=cache)
+        assert not r1["from_cache"] and r1["rows_per_strip"] in (32, 64)
+        assert sum(g > 0 for g in r1["gcups"]) >= 2
+        r2 = sw.sw_db_tune(h, [wl.queries[1]], wl.matrix, 10, 2, cache_path=cache)
+        assert r2["from_cache"] and r2["variant"] == r1["variant"]
+        got = sw.sw_search_batch(h, wl.queries, wl.matrix, 10, 2)
+        assert sw.sw_get_stats(h)["variant"] == r1["variant"]
+    _check(got, exp, "tuned")
+
+
+def test_graph_replay_tracks_query_contents(sw):
+    """A replayed graph rebuilds the query profile from the buffer's current contents."""
+    import torch
+    wl = w.plain(seed=13, scale=0.03)
+    rng = np.random.default_rng(5)
+    q1, q2 = w.draw_residues(rng, 120), w.draw_residues(rng, 120)
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        dq = torch.from_numpy(q1).cuda()
+        out = torch.empty(h.num_seqs, dtype=torch.int32, device="cuda")
+        offs = np.array([0, 120], np.int64)
+        sw.sw_search_batch_device(h, dq, offs, wl.matrix, 10, 2, out)
+        torch.cuda.synchronize()
+        a = out.cpu().numpy().copy()
+        dq.copy_(torch.from_numpy(q2))
+        sw.sw_search_batch_device(h, dq, offs, wl.matrix, 10, 2, out)
+        torch.cuda.synchronize()
+        assert sw.sw_get_stats(h)["graph_replay"] == 1
+        b = out.cpu().numpy().copy()
+    _check(a[None], _oracle_all([q1], wl.db, wl.matrix, 10, 2), "first")
+    _check(b[None], _oracle_all([q2], wl.db, wl.matrix, 10, 2), "replayed")
