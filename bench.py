@@ -53,7 +53,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain", "paper_shaped", "long_subject"])
+                    choices=["batched", "plain", "paper_shaped", "long_subject", "serving"])
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
+    ap.add_argument("--rates", default="0.25,0.5,0.9,1.1",
+                    help="serving: arrival rates as fractions of the measured capacity")
     ap.add_argument("--scale", type=float, default=1.0, help="database scale (tests only)")
     ap.add_argument("--query-lengths", default="",
                     help="comma-separated query lengths replacing the workload's (profiling)")
@@ -75,10 +78,14 @@ WORKLOAD_TEXT = {
                     "sigma 1.0, clip 20..35,000), BLOSUM62, gaps 10/2",
     "long_subject": "5 queries (1,000..5,000) vs 50,000 synthetic sequences uniform over "
                     "5,000..35,000, BLOSUM62, gaps 10/2",
+    "serving": "Poisson arrivals of queries (log-normal lengths mean 400, clip 50..5,000) vs the "
+               "resident 1M-sequence synthetic database (batched config), BLOSUM62, gaps 10/2",
 }
 
 
 def make_workload(name, seed, scale, query_lengths=""):
+    if name == "serving":
+        name = "batched"
     if query_lengths:
         ql = [int(x) for x in query_lengths.split(",") if x]
         return getattr(w, name)(seed=seed, scale=scale, query_lengths=ql)
@@ -148,14 +155,19 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the inter-task kernel from the committed ncu summary, or None
+KERNEL_SRC = {"k_inter_i16x2": INTER_SRC,
+              "k_inter_mq_i16x2": os.path.join(ROOT, "paper_1702_07195_gb300", "csrc",
+                                               "k_inter_mq.cu")}
+
+
+def ncu_traffic(workload, kernel=INTER_KERNEL):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
     if the summary is absent or was taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", f"{INTER_KERNEL}_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    src = hashlib.sha256(open(INTER_SRC, "rb").read()).hexdigest()[:16]
+    src = hashlib.sha256(open(KERNEL_SRC[kernel], "rb").read()).hexdigest()[:16]
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_src or not m_b or m_src.group(1) != src:
@@ -253,9 +265,11 @@ def run_ours(args, world, rank, local):
 
     tune = None
     if not args.no_tune:
-        # probe: the median-length query against the whole database, every kernel variant
-        probe = sorted(wl.queries, key=len)[len(wl.queries) // 2]
-        tune = sw.sw_db_tune(db, [probe], wl.matrix, wl.gap_open, wl.gap_extend)
+        # probe: the two median-length queries (the batch kernel pairs queries) against the
+        # whole database, every kernel variant
+        srt = sorted(wl.queries, key=len)
+        probe = srt[max(0, len(srt) // 2 - 1): len(srt) // 2 + 1]
+        tune = sw.sw_db_tune(db, probe, wl.matrix, wl.gap_open, wl.gap_extend)
 
     def step():
         sw.sw_search_batch_device(db, d_q, qoff, wl.matrix, wl.gap_open, wl.gap_extend, d_s,
@@ -341,11 +355,12 @@ def run_ours(args, world, rank, local):
     peak_gcups = sms * LANE_OPS_PER_CLK_SM * f_max * 2.0 / OPS_PER_CELL_PAIR / 1e9
     st_last = sw.sw_get_stats(db)
     inter_cells = st_last["inter_cells"]
+    kernel_name = "k_inter_mq_i16x2" if st_last.get("multi_query") else INTER_KERNEL
     k_ms = statistics.mean(inter_ms) if inter_ms else float("nan")
     achieved = inter_cells / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
-                "frac": achieved / peak_gcups, "traffic": ncu_traffic(args.workload),
-                "kernel": INTER_KERNEL, "kernel_ms": k_ms,
+                "frac": achieved / peak_gcups, "traffic": ncu_traffic(args.workload, kernel_name),
+                "kernel": kernel_name, "kernel_ms": k_ms,
                 "peak_basis": f"{sms} SMs x {LANE_OPS_PER_CLK_SM} ALU-pipe int16x2 lane-ops/clk x "
                               f"{f_max / 1e6:.0f} MHz x 2 cells / {OPS_PER_CELL_PAIR} DPX ops per "
                               "cell pair (ALU-pipe bound; HBM is not the bound)",
@@ -376,11 +391,74 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_serving(args, world, rank, local):
+    """Continuous-batching server under Poisson arrivals at several rates."""
+    import torch
+    import paper_1702_07195_gb300 as sw
+
+    torch.cuda.set_device(local)
+    wl = make_workload("batched", args.seed + rank, args.scale)
+    db = sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE)
+    R = wl.db.num_residues
+    srv = sw.Server(db, wl.matrix, wl.gap_open, wl.gap_extend, max_inflight=32, slices=8)
+    # capacity: a burst of requests submitted together
+    burst = w.serving_queries(48, seed=args.seed + 100)
+    for t in [srv.submit(q) for q in burst[:8]]:      # warm-up
+        srv.wait(t, 600000)
+    srv.stats(reset=True)
+    t0 = time.perf_counter()
+    for t in [srv.submit(q) for q in burst]:
+        srv.wait(t, 600000)
+    cap_s = time.perf_counter() - t0
+    capacity = len(burst) / cap_s
+    cap_stats = srv.stats(reset=True)
+    results = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for i, frac in enumerate(float(x) for x in args.rates.split(",") if x):
+        rate = frac * capacity
+        qs = w.serving_queries(args.requests, seed=args.seed + 200 + i)
+        arrivals = w.poisson_arrivals(args.requests, rate, seed=args.seed + 300 + i)
+        tickets = []
+        start = time.perf_counter()
+        for a, q in zip(arrivals, qs):
+            delay = start + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(q))
+        for t in tickets:
+            srv.wait(t, 600000)
+        st = srv.stats(reset=True)
+        results.append({"rate_frac": frac, "rate_rps": rate, "requests": args.requests,
+                        "p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"],
+                        "mean_ms": st["latency_mean_ms"], "gcups": st["gcups"],
+                        "max_in_flight": st["max_in_flight"],
+                        "joined_while_running": st["joined_while_running"],
+                        "ticks": st["ticks"]})
+    clocks = sampler.stop()
+    srv.close()
+    db.close()
+    best = max((r for r in results if r["rate_frac"] <= 1.0), key=lambda r: r["gcups"],
+               default=results[-1] if results else {"gcups": 0.0})
+    line = {"metric": "GCUPS (served)", "value": best["gcups"], "unit": "GCUPS", "n_gpus": world,
+            "steps": len(results), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (int32 rescore)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["serving"], "db_seqs": wl.db.num_seqs,
+                       "db_residues": R, "max_inflight": 32, "slices": 8,
+                       "capacity_rps": capacity, "capacity_gcups": cap_stats["gcups"]},
+            "serving": results, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "serving":
+        run_serving(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -76,6 +76,8 @@ typedef struct {
     int32_t inter_block;   /* threads per block of the inter-task kernel */
     int32_t graph_replay;  /* 1 if the launch sequence was a replayed CUDA graph */
     int32_t variant;       /* inter-task kernel variant used (see sw_db_tune) */
+    int32_t multi_query;   /* 1 if two queries shared each register (two or more queries) */
+    int32_t reserved;
 } sw_stats;
 
 /* ---------------------------------------------------------------- database ------------ */
@@ -146,6 +148,53 @@ sw_status sw_db_set_variant(sw_db *db, int32_t variant);
 
 /* Measurements of the last completed search on `db` (synchronises the handle's stream). */
 sw_status sw_get_stats(const sw_db *db, sw_stats *out);
+
+/* ---------------------------------------------------------------- serving ------------- */
+
+/* Continuous-batching search server over a resident database (the paper searches one query
+ * at a time; serving is this library's addition).  Requests (one query each) are admitted
+ * while a slot is free and their DP state fits the budget; DP state of a request = its query
+ * profile ((A+1) x ceil(m/256)*256 int16) plus its score row (num_seqs int32).  A background
+ * thread runs "ticks": each tick is one replay of a captured CUDA graph in which every
+ * in-flight request processes its next share of database chunks (a request admitted while
+ * others are running joins at the next tick and shares the same launches), followed by the
+ * int32 work (long subjects of newly admitted requests, saturated lanes).  A request
+ * completes when its last chunk is done; its scores (original order) are then copied to the
+ * host.  Each score equals the one sw_search returns for the same query.
+ * Gap costs must fit the int16 path (gap_open, gap_extend <= 16383). */
+typedef struct {
+    int32_t max_inflight;        /* requests on the GPU at once (default 32, max 128) */
+    int32_t max_query_len;       /* longest accepted query (default 8192) */
+    int64_t state_budget_bytes;  /* DP-state bytes of all in-flight requests (default 1 GiB) */
+    int32_t slices;              /* a request's chunks are served in at least this many
+                                    shares when the server is busy (default 8) */
+    int32_t max_pending;         /* submitted but not admitted (default 4096) */
+    int32_t reserved[6];
+} sw_server_options;
+
+typedef struct {
+    int64_t submitted, completed, rejected, ticks;
+    int32_t in_flight, max_in_flight;
+    int64_t joined_while_running; /* admissions while other requests were in flight */
+    double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms;
+    double gcups;                 /* cells of completed requests / (last completion - first submit) */
+    int64_t cells;
+} sw_server_stats;
+
+sw_status sw_server_create(sw_db *db, const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                           const sw_server_options *opts, sw_server **out);
+/* Copies the query; returns a ticket.  SW_ERR_BUSY if max_pending requests are waiting. */
+sw_status sw_server_submit(sw_server *srv, const uint8_t *query, int32_t query_len,
+                           int64_t *ticket);
+/* If the request is done, copies its num_seqs scores to `scores`, sets *done = 1 and retires
+ * the ticket; otherwise sets *done = 0. */
+sw_status sw_server_poll(sw_server *srv, int64_t ticket, int32_t *scores, int32_t *done);
+/* Waits up to timeout_ms (bounded; SW_ERR_TIMEOUT) for the request, then as sw_server_poll. */
+sw_status sw_server_wait(sw_server *srv, int64_t ticket, int32_t *scores, int32_t timeout_ms);
+/* Counters and latency percentiles of completed requests (reset = 1 clears them). */
+sw_status sw_server_get_stats(sw_server *srv, sw_server_stats *out, int32_t reset);
+/* Stops the loop (in-flight work finishes first) and frees the server. */
+void sw_server_destroy(sw_server *srv);
 
 /* ---------------------------------------------------------------- host-side plan ------ */
 

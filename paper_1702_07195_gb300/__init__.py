@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
                 ("cells", ctypes.c_int64), ("inter_cells", ctypes.c_int64),
                 ("flagged", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("inter_grid", ctypes.c_int32), ("inter_block", ctypes.c_int32),
-                ("graph_replay", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("graph_replay", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("multi_query", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -57,6 +58,25 @@ class TuneResult(ctypes.Structure):
         return {"variant": self.variant, "rows_per_strip": self.rows_per_strip,
                 "warps_per_block": self.warps_per_block, "from_cache": bool(self.from_cache),
                 "gcups": [round(float(x), 1) for x in self.gcups[:self.num_variants]]}
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("max_query_len", ctypes.c_int32),
+                ("state_budget_bytes", ctypes.c_int64), ("slices", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("in_flight", ctypes.c_int32), ("max_in_flight", ctypes.c_int32),
+                ("joined_while_running", ctypes.c_int64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+                ("gcups", ctypes.c_double), ("cells", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -94,6 +114,13 @@ def _load():
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                                       ctypes.c_int32, ctypes.POINTER(TuneResult)]),
         "sw_db_set_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
+        "sw_server_create": (ctypes.c_int, [_vp, _i8p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(ServerOptions), ctypes.POINTER(_vp)]),
+        "sw_server_submit": (ctypes.c_int, [_vp, _u8p, ctypes.c_int32, _i64p]),
+        "sw_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, _i32p]),
+        "sw_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, ctypes.c_int32]),
+        "sw_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats), ctypes.c_int32]),
+        "sw_server_destroy": (None, [_vp]),
         "sw_last_error": (ctypes.c_char_p, []),
         "sw_version": (ctypes.c_char_p, []),
         "sw_launch_count": (ctypes.c_int64, []),
@@ -309,3 +336,60 @@ def sw_layout(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 307
                                _ptr(perm, _i32p), _ptr(inter, _u8p), _ptr(lids, _i32p)))
     return {"group_off": goff[:ng.value], "group_len": glen[:ng.value],
             "perm": perm[:ng.value * 64], "inter": inter[:nb.value], "long_ids": lids[:nl.value]}
+
+
+class Server:
+    """Continuous-batching search server over a resident database (``sw_server_*``)."""
+
+    def __init__(self, db: Database, matrix, gap_open: int, gap_extend: int,
+                 max_inflight: int = 0, max_query_len: int = 0, state_budget_bytes: int = 0,
+                 slices: int = 0, max_pending: int = 0):
+        self.db = db
+        m = _matrix(matrix)
+        opts = ServerOptions()
+        opts.max_inflight, opts.max_query_len = int(max_inflight), int(max_query_len)
+        opts.state_budget_bytes, opts.slices = int(state_budget_bytes), int(slices)
+        opts.max_pending = int(max_pending)
+        h = _vp()
+        _check(lib.sw_server_create(db.handle, _ptr(m, _i8p), int(gap_open), int(gap_extend),
+                                    ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, query) -> int:
+        q = _u8(query)
+        t = ctypes.c_int64()
+        _check(lib.sw_server_submit(self._h, _ptr(q, _u8p), int(q.shape[0]), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        out = np.empty(self.db.num_seqs, dtype=np.int32)
+        done = ctypes.c_int32()
+        _check(lib.sw_server_poll(self._h, int(ticket), _ptr(out, _i32p), ctypes.byref(done)))
+        return out if done.value else None
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> np.ndarray:
+        out = np.empty(self.db.num_seqs, dtype=np.int32)
+        _check(lib.sw_server_wait(self._h, int(ticket), _ptr(out, _i32p), int(timeout_ms)))
+        return out
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(lib.sw_server_get_stats(self._h, ctypes.byref(st), int(reset)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sw_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -36,17 +36,19 @@ struct Pair {
 
 // Claims the next (query, subject) pair of the long or all-pairs work sources.
 __device__ __forceinline__ bool next_enumerated(const IntraParams& p, int lane, Pair& out) {
-    const int64_t nsub = (p.mode == kIntraLong) ? p.num_long : p.num_seqs;
+    const bool tick = p.mode == kIntraTickLong;
+    const int64_t nsub = (p.mode == kIntraLong || tick) ? p.num_long : p.num_seqs;
+    const int64_t nq = tick ? p.tick->n_long : p.num_queries;
     const unsigned long long total =
-        static_cast<unsigned long long>(nsub) * static_cast<unsigned long long>(p.num_queries);
+        static_cast<unsigned long long>(nsub) * static_cast<unsigned long long>(nq);
     unsigned long long k = 0;
     if (lane == 0) k = atomicAdd(&p.ctrl->next_intra, 1ull);
     k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= total) return false;
-    const int64_t si = static_cast<int64_t>(k / static_cast<unsigned long long>(p.num_queries));
-    const int qi = static_cast<int>(static_cast<int64_t>(k) - si * p.num_queries);
-    out.q = p.query_order[qi];
-    out.seq = (p.mode == kIntraLong) ? p.long_ids[si] : static_cast<int>(si);
+    const int64_t si = static_cast<int64_t>(k / static_cast<unsigned long long>(nq));
+    const int qi = static_cast<int>(static_cast<int64_t>(k) - si * nq);
+    out.q = tick ? p.tick->long_slot[qi] : p.query_order[qi];
+    out.seq = (p.mode == kIntraLong || tick) ? p.long_ids[si] : static_cast<int>(si);
     return true;
 }
 

@@ -56,6 +56,11 @@ bool graphs_enabled() {
     return !(v && v[0] == '0');
 }
 
+bool mq_enabled() {
+    const char* v = std::getenv("SWGB_MQ");
+    return !(v && v[0] == '0');
+}
+
 }  // namespace
 
 namespace swgb {
@@ -160,8 +165,51 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     P.num_items = static_cast<int64_t>(items.size());
     if (P.num_items > INT32_MAX) return fail(SW_ERR_ARG, "too many work items");
 
+    // Two or more queries: pair them two per register (multi-query kernel).  Queries go, strip
+    // by strip, into two streams balanced by strip count, longest first.
+    int nonempty = 0;
+    for (int q = 0; q < nq; ++q) nonempty += P.m[static_cast<size_t>(q)] > 0;
+    std::vector<MqStep> steps;
+    const int mqT = inter_mq_variant_rows(P.variant);
+    P.mq = mq_enabled() && P.int16_ok && G > 0 && nonempty >= 2 &&
+           db->inter_mq_occ[P.variant] > 0;
+    if (P.mq) {
+        std::vector<int32_t> stream[2];
+        int64_t len[2] = {0, 0};
+        for (int32_t q : order) {
+            const int32_t mq = P.m[static_cast<size_t>(q)];
+            if (mq == 0) continue;
+            const int x = len[0] <= len[1] ? 0 : 1;
+            stream[x].push_back(q);
+            len[x] += (mq + mqT - 1) / mqT;
+        }
+        P.num_steps = static_cast<int32_t>(std::max(len[0], len[1]));
+        steps.assign(static_cast<size_t>(P.num_steps), MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0});
+        for (int x = 0; x < 2; ++x) {
+            int64_t k = 0;
+            for (int32_t q : stream[x]) {
+                const int32_t S = (P.m[static_cast<size_t>(q)] + mqT - 1) / mqT;
+                for (int32_t sidx = 0; sidx < S; ++sidx, ++k) {
+                    MqStep& st = steps[static_cast<size_t>(k)];
+                    uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
+                    if (sidx == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
+                    if (sidx == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
+                    st.flags = fl;
+                    if (x == 0) {
+                        st.qa = q;
+                        st.sa = sidx;
+                    } else {
+                        st.qb = q;
+                        st.sb = sidx;
+                    }
+                }
+            }
+        }
+        P.rows_pad = round_up(static_cast<int64_t>(P.num_steps) * mqT, kQpRows);
+    }
+
     // Scratch shared by all plans of this database.
-    P.inter_grid = db->sms * std::max(1, db->inter_occ[P.variant]);
+    P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]);
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
     const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
@@ -181,6 +229,10 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     CU(P.qoff.ensure(static_cast<size_t>(nq) + 1));
     CU(P.order.ensure(static_cast<size_t>(nq)));
     CU(P.matrix.ensure(static_cast<size_t>(A * A)));
+    if (P.mq) {
+        CU(P.steps.ensure(steps.size()));
+        CU(P.pp.ensure(static_cast<size_t>((A + 1) * P.rows_pad)));
+    }
     std::vector<QueryDesc> descs(static_cast<size_t>(nq));
     for (int q = 0; q < nq; ++q)
         descs[static_cast<size_t>(q)] = QueryDesc{P.qp.ptr + qp_off[static_cast<size_t>(q)],
@@ -196,6 +248,9 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     CU(cudaMemcpyAsync(P.qoff.ptr, h_qoff, sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, us));
     CU(cudaMemcpyAsync(P.order.ptr, order.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, us));
     CU(cudaMemcpyAsync(P.matrix.ptr, h_matrix, static_cast<size_t>(A * A), cudaMemcpyHostToDevice, us));
+    if (P.mq)
+        CU(cudaMemcpyAsync(P.steps.ptr, steps.data(), sizeof(MqStep) * steps.size(),
+                           cudaMemcpyHostToDevice, us));
     CU(cudaStreamSynchronize(us));
 
     const Gaps gaps{goe, ge, std::min(goe, ge)};
@@ -215,6 +270,27 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     ip.bnd = db->bnd.ptr;
     ip.bnd_stride = bnd_stride;
     ip.gaps = gaps;
+    if (P.mq) {
+        InterMqParams& mp = P.inter_mq;
+        mp.inter = db->inter.ptr;
+        mp.group_off = db->group_off.ptr;
+        mp.group_len = db->group_len.ptr;
+        mp.perm = db->perm.ptr;
+        mp.queries = P.descs.ptr;
+        mp.pp = P.pp.ptr;
+        mp.rows_pad = P.rows_pad;
+        mp.steps = P.steps.ptr;
+        mp.num_steps = P.num_steps;
+        mp.num_half_groups = static_cast<int32_t>(2 * G);
+        mp.alphabet1 = A + 1;
+        mp.ctrl = db->ctrl.ptr;
+        mp.flags = db->flags.ptr;
+        mp.flag_cap = P.flag_cap;
+        mp.thresh = ip.thresh;
+        mp.bnd = db->bnd.ptr;
+        mp.bnd_stride = bnd_stride;
+        mp.gaps = gaps;
+    }
     IntraParams& jp = P.intra;
     jp.plain = db->plain.ptr;
     jp.plain_off = db->plain_off.ptr;
@@ -271,7 +347,13 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
                        P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
     ++launches;
     CU(record(db->ev[1], st));
-    if (P.num_items > 0) {
+    if (P.mq) {
+        CU(launch_build_pp(d_queries, P.qoff.ptr, P.steps.ptr, P.num_steps,
+                           inter_mq_variant_rows(P.variant), P.matrix.ptr, db->A, P.qp_bias,
+                           P.pp.ptr, P.rows_pad, db->ctrl.ptr, st));
+        CU(launch_inter_mq(P.inter_mq, P.variant, P.inter_grid, st));
+        launches += 2;
+    } else if (P.num_items > 0) {
         CU(launch_inter(P.inter, P.variant, P.inter_grid, st));
         ++launches;
     }
@@ -333,6 +415,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(gap_open);
     key.push_back(gap_extend);
     key.push_back(db->variant);
+    key.push_back(mq_enabled() ? 1 : 0);
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 
@@ -381,6 +464,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     db->stats.launches = plan->launches;
     db->stats.inter_grid = plan->inter_grid;
     db->stats.inter_block = inter_variant_warps(plan->variant) * kWarp;
+    db->stats.multi_query = plan->mq ? 1 : 0;
     db->stats.graph_replay = replay ? 1 : 0;
     db->stats.variant = plan->variant;
     db->stats_pending = true;
@@ -509,6 +593,8 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     CU(cudaDeviceGetAttribute(&db->sms, cudaDevAttrMultiProcessorCount, dev));
     for (int v = 0; v < inter_num_variants() && v < kMaxVariants; ++v)
         db->inter_occ[v] = inter_occupancy(v, alphabet_size + 1);
+    for (int v = 0; v < inter_mq_num_variants() && v < kMaxVariants; ++v)
+        db->inter_mq_occ[v] = inter_mq_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);

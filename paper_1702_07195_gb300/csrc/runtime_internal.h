@@ -74,6 +74,13 @@ struct Plan {
     DevBuf<int8_t> matrix;
     InterParams inter{};
     IntraParams intra{};
+    // multi-query kernel (two queries per register against one subject)
+    bool mq = false;
+    int32_t num_steps = 0;
+    int64_t rows_pad = 0;
+    DevBuf<MqStep> steps;
+    DevBuf<uint32_t> pp;
+    InterMqParams inter_mq{};
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -111,6 +118,7 @@ struct sw_db {
     // kernel choice
     int variant = 0;
     int inter_occ[swgb::kMaxVariants] = {};
+    int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;
     // last search
     sw_stats stats{};

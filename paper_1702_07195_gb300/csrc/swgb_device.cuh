@@ -39,6 +39,19 @@ struct InterItem {
     int32_t cost;        // unused on the device; the host sorts by it
 };
 
+// One tick of the serving loop (continuous batching): every in-flight request contributes a
+// range of its database chunks (W groups each); requests admitted this tick also get their
+// long subjects.  Uploaded to the device before each replay of the tick graph.
+constexpr int kTickMax = 128;
+struct TickDesc {
+    int32_t n;                        // requests in this tick
+    int32_t n_long;                   // requests whose long subjects run in this tick
+    int32_t slot[kTickMax];           // query slot of request s
+    int32_t chunk_end[kTickMax];      // its chunks [chunk_end - count, chunk_end), longest first
+    int32_t prefix[kTickMax + 1];     // item offsets: request s owns items [prefix[s], prefix[s+1])
+    int32_t long_slot[kTickMax];
+};
+
 struct FlagEntry {
     int32_t query;
     int32_t seq;
@@ -76,13 +89,48 @@ struct InterParams {
     uint4* bnd;          // strip-boundary buffers, one per resident warp
     int64_t bnd_stride;  // uint4 per warp slot
     Gaps gaps;
+    const TickDesc* tick;   // non-null: items come from this tick descriptor, not `items`
+    int32_t num_groups;     // groups in the database (tick mode)
+};
+
+// Multi-query inter-task kernel: the two int16 lanes of a register hold two different queries
+// against the same subject.  The queries are laid out in two "streams" of T-row strips; step k
+// pairs strip k of stream a (lane a) with strip k of stream b (lane b).
+struct MqStep {
+    int32_t qa, qb;      // query slots (-1: the lane has no query at this step)
+    int32_t sa, sb;      // strip index within that query
+    uint32_t flags;      // kMqFirstA | kMqLastA | kMqFirstB | kMqLastB
+    int32_t pad;
+};
+constexpr uint32_t kMqFirstA = 1u, kMqLastA = 2u, kMqFirstB = 4u, kMqLastB = 8u;
+
+struct InterMqParams {
+    const uint8_t* inter;
+    const int64_t* group_off;
+    const int32_t* group_len;
+    const int32_t* perm;
+    const QueryDesc* queries;   // output rows (qp unused)
+    const uint32_t* pp;         // paired profile: pp[d * rows_pad + k * T + r] = (S'_a, S'_b)
+    int64_t rows_pad;           // multiple of kQpRows
+    const MqStep* steps;
+    int32_t num_steps;
+    int32_t num_half_groups;    // 2 x groups: each warp item is one slot parity of one group
+    int32_t alphabet1;
+    Control* ctrl;
+    FlagEntry* flags;
+    uint32_t flag_cap;
+    int32_t thresh;
+    uint4* bnd;
+    int64_t bnd_stride;
+    Gaps gaps;
 };
 
 // Work source of the int32 intra-task kernel.
 enum IntraMode : int32_t {
     kIntraLong = 0,      // (query, long subject) pairs: num_queries x num_long
     kIntraRescore = 1,   // entries of the saturation list, then a sweep if it overflowed
-    kIntraAll = 2        // every (query, sequence) pair (int16 path not applicable)
+    kIntraAll = 2,       // every (query, sequence) pair (int16 path not applicable)
+    kIntraTickLong = 3   // serving: long subjects of the requests admitted in this tick
 };
 
 struct IntraParams {
@@ -103,6 +151,7 @@ struct IntraParams {
     int64_t spill_stride;       // int2 per warp slot
     Gaps gaps;
     int32_t qp_add;             // Goe minus the profile's bias (0 unless Goe is too large)
+    const TickDesc* tick;       // kIntraTickLong
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -117,6 +166,16 @@ int inter_variant_warps(int variant);
 size_t inter_smem_bytes(int alphabet1);
 int inter_occupancy(int variant, int alphabet1);
 cudaError_t launch_inter(const InterParams& p, int variant, int grid, cudaStream_t st);
+int inter_mq_num_variants();
+int inter_mq_variant_rows(int variant);
+int inter_mq_variant_warps(int variant);
+size_t inter_mq_smem_bytes(int alphabet1);
+int inter_mq_occupancy(int variant, int alphabet1);
+cudaError_t launch_inter_mq(const InterMqParams& p, int variant, int grid, cudaStream_t st);
+cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, const MqStep* d_steps,
+                            int32_t num_steps, int32_t rows_per_strip, const int8_t* d_matrix,
+                            int32_t A, int32_t bias, uint32_t* d_pp, int64_t rows_pad,
+                            Control* ctrl, cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
 int intra_block_threads();
 int intra_rows_per_pass();

@@ -256,3 +256,27 @@ def test_graph_replay_tracks_query_contents(sw):
         b = out.cpu().numpy().copy()
     _check(a[None], _oracle_all([q1], wl.db, wl.matrix, 10, 2), "first")
     _check(b[None], _oracle_all([q2], wl.db, wl.matrix, 10, 2), "replayed")
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_multi_query_kernel_matches_oracle(sw, variant, monkeypatch):
+    """Two queries per register (multi-query kernel): ragged query lengths around the strip
+    height, an empty query in the batch, an odd count, and planted int16 saturation, for every
+    variant; the same batch with the multi-query path switched off agrees."""
+    rng = np.random.default_rng(100 + variant)
+    base = w.batched(seed=14, scale=0.003).db
+    db2, q_sat, _ = w.plant_saturating(base, w.draw_residues(rng, 20), count=3, run=3100)
+    lens = [31, 32, 33, 0, 63, 65, 200, 1, 129]
+    qs = [w.draw_residues(rng, n) for n in lens] + [q_sat]
+    sm = w.blosum62()
+    exp = _oracle_all(qs, db2, sm, 10, 2)
+    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, long_cutoff=4096) as h:
+        sw.sw_db_set_variant(h, variant)
+        got = sw.sw_search_batch(h, qs, sm, 10, 2)
+        st = sw.sw_get_stats(h)
+        assert st["multi_query"] == 1 and st["flagged"] >= 3
+        _check(got, exp, f"multi-query variant {variant}")
+        monkeypatch.setenv("SWGB_MQ", "0")
+        got2 = sw.sw_search_batch(h, qs, sm, 10, 2)
+        assert sw.sw_get_stats(h)["multi_query"] == 0
+    _check(got2, exp, "single-query kernel")
