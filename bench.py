@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="force an inter-task kernel variant instead of autotuning (profiling)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the one-query-per-launch comparison")
     return ap.parse_args()
 
 
@@ -264,7 +268,10 @@ def run_ours(args, world, rank, local):
     cells = int(cat.size) * wl.db.num_residues
 
     tune = None
-    if not args.no_tune:
+    if args.variant >= 0:
+        sw.sw_db_set_variant(db, args.variant)
+        tune = {"variant": args.variant, "forced": True}
+    elif not args.no_tune:
         # probe: the two median-length queries (the batch kernel pairs queries) against the
         # whole database, every kernel variant
         srt = sorted(wl.queries, key=len)
@@ -344,6 +351,29 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(cat.size + mat.size),
                "d2h_bytes_per_step": int(nq * N * 4)}
 
+    # the same queries, one query per launch (the "plain" search): same kernels, no batching
+    plain = None
+    if not args.no_plain and nq > 1:
+        offs1 = [np.array([0, len(q)], np.int64) for q in wl.queries]
+        d_qs = [torch.from_numpy(q).cuda() for q in wl.queries]
+        d_s1 = torch.empty(N, dtype=torch.int32, device="cuda")
+
+        def plain_step():
+            for dq, o in zip(d_qs, offs1):
+                sw.sw_search_batch_device(db, dq, o, wl.matrix, wl.gap_open, wl.gap_extend, d_s1,
+                                          stream=stream)
+
+        plain_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p_ms = e0.elapsed_time(e1)
+        plain = {"gcups": cells / (p_ms * 1e-3) / 1e9, "ms_per_pass": p_ms,
+                 "what": "the same queries, one per launch (single-query kernel)"}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -379,6 +409,7 @@ def run_ours(args, world, rank, local):
                        "l2": f"inputs larger than L2 (database {wl.db.num_residues / 1e6:.0f} MB "
                              "resident in HBM, read once per query per step)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+            "plain_one_query_per_launch": plain,
             "flagged_lanes_per_step": flagged / max(1, args.steps)}
     if e2e:
         line["e2e"] = e2e

@@ -314,7 +314,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         if (P.int16_ok)
             P.inter_cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * db->layout.short_residues;
     }
-    if (db->plans.size() >= 8) {
+    if (db->plans.size() >= 32) {
         if (db->done_recorded) cudaEventSynchronize(db->ev[4]);   // its graph may still run
         if (db->plans.front()->exec) cudaGraphExecDestroy(db->plans.front()->exec);
         db->plans.erase(db->plans.begin());

@@ -114,7 +114,7 @@ struct sw_db {
     cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
     cudaEvent_t ev[5] = {};                  // per-kernel timing; ev[4] = end of the last search
     bool done_recorded = false;
-    std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 8
+    std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 32
     // kernel choice
     int variant = 0;
     int inter_occ[swgb::kMaxVariants] = {};
