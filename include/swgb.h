@@ -149,25 +149,38 @@ sw_status sw_db_set_variant(sw_db *db, int32_t variant);
 /* Measurements of the last completed search on `db` (synchronises the handle's stream). */
 sw_status sw_get_stats(const sw_db *db, sw_stats *out);
 
+/* ---------------------------------------------------------------- sorting stage ------- */
+
+/* Sorting stage (paper Section 4, step 3: alignment scores sorted in descending order), as a
+ * top-k: for each of num_queries score rows on the device (row q = d_scores + q * num_seqs,
+ * scores >= 0 as the searches return them), the k best database sequences in descending
+ * score order, equal scores by ascending sequence index.  Outputs on the device:
+ * d_top_scores[q * k + r] and d_top_ids[q * k + r], r = 0 .. k-1.  k <= SW_TOPK_MAX and
+ * k <= num_seqs.  Enqueued on `stream` (NULL = legacy default stream). */
+#define SW_TOPK_MAX 4096
+sw_status sw_topk(const int32_t *d_scores, int64_t num_seqs, int32_t num_queries, int32_t k,
+                  int32_t *d_top_scores, int32_t *d_top_ids, void *stream);
+
 /* ---------------------------------------------------------------- serving ------------- */
 
 /* Continuous-batching search server over a resident database (the paper searches one query
  * at a time; serving is this library's addition).  Requests (one query each) are admitted
  * while a slot is free and their DP state fits the budget; DP state of a request = its query
- * profile ((A+1) x ceil(m/256)*256 int16) plus its score row (num_seqs int32).  A background
- * thread runs "ticks": each tick is one replay of a captured CUDA graph in which every
- * in-flight request processes its next share of database chunks (a request admitted while
- * others are running joins at the next tick and shares the same launches), followed by the
- * int32 work (long subjects of newly admitted requests, saturated lanes).  A request
- * completes when its last chunk is done; its scores (original order) are then copied to the
+ * profile ((A+1) x ceil(m/256)*256 int16) plus its score row (num_seqs int32).  The database
+ * is cut into `slices` of about equal residue work; a background thread runs "ticks" that scan
+ * the slices cyclically.  In a tick every in-flight request aligns against the current slice:
+ * one replay of a captured CUDA graph, with two queries per int16x2 register when two or more
+ * requests are in flight, followed by the int32 work (long subjects of newly admitted
+ * requests, saturated lanes).  A request admitted while others run joins at the next tick and
+ * completes after one full cycle of slices; its scores (original order) are then copied to the
  * host.  Each score equals the one sw_search returns for the same query.
  * Gap costs must fit the int16 path (gap_open, gap_extend <= 16383). */
 typedef struct {
     int32_t max_inflight;        /* requests on the GPU at once (default 32, max 128) */
     int32_t max_query_len;       /* longest accepted query (default 8192) */
     int64_t state_budget_bytes;  /* DP-state bytes of all in-flight requests (default 1 GiB) */
-    int32_t slices;              /* a request's chunks are served in at least this many
-                                    shares when the server is busy (default 8) */
+    int32_t slices;              /* database slices of the cyclic scan; a request takes one
+                                    tick per slice (default 8) */
     int32_t max_pending;         /* submitted but not admitted (default 4096) */
     int32_t reserved[6];
 } sw_server_options;

@@ -121,6 +121,8 @@ def _load():
         "sw_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, ctypes.c_int32]),
         "sw_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats), ctypes.c_int32]),
         "sw_server_destroy": (None, [_vp]),
+        "sw_topk": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                   _vp]),
         "sw_last_error": (ctypes.c_char_p, []),
         "sw_version": (ctypes.c_char_p, []),
         "sw_launch_count": (ctypes.c_int64, []),
@@ -306,6 +308,25 @@ def sw_db_tune(db: Database, queries, matrix, gap_open: int, gap_extend: int,
 
 def sw_db_set_variant(db: Database, variant: int) -> None:
     _check(lib.sw_db_set_variant(db.handle, int(variant)))
+
+
+def sw_topk(d_scores, num_seqs: int, num_queries: int, k: int, stream=None):
+    """Sorting stage: per query, the k best (score, index) pairs, descending score, ties by
+    ascending index.  d_scores: int32 CUDA tensor (num_queries * num_seqs).  Returns two int32
+    CUDA tensors of shape (num_queries, k)."""
+    import torch
+    if d_scores.dtype != torch.int32 or not d_scores.is_cuda or not d_scores.is_contiguous():
+        raise ValueError("d_scores must be a contiguous int32 CUDA tensor")
+    if d_scores.numel() < num_queries * num_seqs:
+        raise ValueError("d_scores too small")
+    top_s = torch.empty((num_queries, k), dtype=torch.int32, device=d_scores.device)
+    top_i = torch.empty((num_queries, k), dtype=torch.int32, device=d_scores.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(d_scores.device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.sw_topk(_vp(d_scores.data_ptr()), int(num_seqs), int(num_queries), int(k),
+                       _vp(top_s.data_ptr()), _vp(top_i.data_ptr()), _vp(s)))
+    return top_s, top_i
 
 
 def sw_get_stats(db: Database) -> dict:

@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
     k.nge = pack2mq(-p.gaps.ge);
     k.ngep = pack2mq(-p.gaps.gep);
     k.floor = 0x80008000u;
-    const int num_items = (p.num_half_groups + kW - 1) / kW;
+    const int num_steps = p.tick ? p.tick->mq_steps : p.num_steps;
+    const int hg_begin = p.tick ? p.tick->hg_begin : 0;
+    const int hg_end = p.tick ? p.tick->hg_end : p.num_half_groups;
+    const int num_items = (hg_end - hg_begin + kW - 1) / kW;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_inter, 1u));
@@ -144,15 +147,15 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
         __syncthreads();
         if (it >= num_items) break;
         // longest groups first: half-groups are in ascending length order
-        const int hg = (num_items - 1 - it) * kW + warp;
-        const bool active = hg < p.num_half_groups;
+        const int hg = hg_begin + (num_items - 1 - it) * kW + warp;
+        const bool active = hg < hg_end;
         const int g = hg >> 1, h = hg & 1;
         const int L = active ? p.group_len[g] : 0;
         const uint4* res =
             active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
         const int id = active ? p.perm[g * kGroupSeqs + 2 * lane + h] : -1;
         unsigned best = 0;
-        for (int k0 = 0; k0 < p.num_steps; k0 += kStepsPerChunk) {
+        for (int k0 = 0; k0 < num_steps; k0 += kStepsPerChunk) {
             __syncthreads();
             constexpr int kVecPerRow = kChunk / 4;
             const int64_t row0 = static_cast<int64_t>(k0) * kT;
@@ -164,13 +167,13 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
             }
             __syncthreads();
             if (!active || L == 0) continue;
-            const int k_end = min(p.num_steps, k0 + kStepsPerChunk);
+            const int k_end = min(num_steps, k0 + kStepsPerChunk);
             for (int ks = k0; ks < k_end; ++ks) {
                 const MqStep st = p.steps[ks];
                 const bool fa = st.flags & kMqFirstA, fb = st.flags & kMqFirstB;
                 const unsigned keep = (fa ? 0u : 0x0000FFFFu) | (fb ? 0u : 0xFFFF0000u);
                 strip_mq<kT>(res, L, h, bnd, s_pp + (ks - k0) * kT, pstride, keep,
-                             keep != 0u, ks + 1 < p.num_steps, k, best, lane);
+                             keep != 0u, ks + 1 < num_steps, k, best, lane);
                 if (st.flags & kMqLastA) {
                     emit_mq(p, st.qa, id, static_cast<int>(static_cast<short>(best & 0xFFFFu)));
                     best &= 0xFFFF0000u;
@@ -200,12 +203,14 @@ constexpr int kNumMq = sizeof(kMqVariants) / sizeof(kMqVariants[0]);
 // Paired profile: pp[d * rows_pad + k*T + r] = (S'(qa, sa*T + r, d), S'(qb, sb*T + r, d)) with
 // S' = SM + bias, and 0 + bias for the dummy code, rows past a query's end and absent lanes.
 __global__ void k_build_pp(const uint8_t* __restrict__ queries, const int64_t* __restrict__ qoff,
-                           const MqStep* __restrict__ steps, int32_t num_steps, int32_t T,
+                           const int32_t* __restrict__ qlen, const MqStep* __restrict__ steps,
+                           int32_t num_steps_arg, const TickDesc* __restrict__ tick, int32_t T,
                            const int8_t* __restrict__ matrix, int32_t A, int32_t bias,
                            uint32_t* __restrict__ pp, int64_t rows_pad, Control* ctrl) {
     const int d = blockIdx.y;
     const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (row >= rows_pad) return;
+    const int32_t num_steps = tick ? tick->mq_steps : num_steps_arg;
     const int64_t ks = row / T;
     const int r = static_cast<int>(row - ks * T);
     int sa = 0, sb = 0;
@@ -218,7 +223,7 @@ __global__ void k_build_pp(const uint8_t* __restrict__ queries, const int64_t* _
             const int q = qs[l];
             if (q < 0 || d >= A) continue;
             const int64_t q0 = qoff[q];
-            const int64_t m = qoff[q + 1] - q0;
+            const int64_t m = qlen ? qlen[q] : qoff[q + 1] - q0;
             const int64_t i = static_cast<int64_t>(strips[l]) * T + r;
             if (i >= m) continue;
             const int code = queries[q0 + i];
@@ -277,14 +282,15 @@ cudaError_t launch_inter_mq(const InterMqParams& p, int variant, int grid, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, const MqStep* d_steps,
-                            int32_t num_steps, int32_t rows_per_strip, const int8_t* d_matrix,
-                            int32_t A, int32_t bias, uint32_t* d_pp, int64_t rows_pad,
-                            Control* ctrl, cudaStream_t st) {
+cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, const int32_t* d_qlen,
+                            const MqStep* d_steps, int32_t num_steps, const TickDesc* tick,
+                            int32_t rows_per_strip, const int8_t* d_matrix, int32_t A,
+                            int32_t bias, uint32_t* d_pp, int64_t rows_pad, Control* ctrl,
+                            cudaStream_t st) {
     const int threads = 256;
     dim3 grid(static_cast<unsigned>((rows_pad + threads - 1) / threads), static_cast<unsigned>(A + 1));
-    k_build_pp<<<grid, threads, 0, st>>>(d_queries, d_qoff, d_steps, num_steps, rows_per_strip,
-                                         d_matrix, A, bias, d_pp, rows_pad, ctrl);
+    k_build_pp<<<grid, threads, 0, st>>>(d_queries, d_qoff, d_qlen, d_steps, num_steps, tick,
+                                         rows_per_strip, d_matrix, A, bias, d_pp, rows_pad, ctrl);
     return cudaGetLastError();
 }
 

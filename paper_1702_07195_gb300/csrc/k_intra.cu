@@ -36,6 +36,24 @@ struct Pair {
 
 // Claims the next (query, subject) pair of the long or all-pairs work sources.
 __device__ __forceinline__ bool next_enumerated(const IntraParams& p, int lane, Pair& out) {
+    if (p.mode == kIntraGroups) {   // layout slots, longest groups first, fillers skipped
+        const int64_t nslots = p.slot_end - p.slot_begin;
+        const unsigned long long total =
+            static_cast<unsigned long long>(nslots) * static_cast<unsigned long long>(p.num_queries);
+        for (;;) {
+            unsigned long long k = 0;
+            if (lane == 0) k = atomicAdd(&p.ctrl->next_groups, 1ull);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= total) return false;
+            const int64_t si = static_cast<int64_t>(k / static_cast<unsigned long long>(p.num_queries));
+            const int qi = static_cast<int>(static_cast<int64_t>(k) - si * p.num_queries);
+            const int id = p.perm[p.slot_end - 1 - si];
+            if (id < 0) continue;
+            out.q = p.query_order[qi];
+            out.seq = id;
+            return true;
+        }
+    }
     const bool tick = p.mode == kIntraTickLong;
     const int64_t nsub = (p.mode == kIntraLong || tick) ? p.num_long : p.num_seqs;
     const int64_t nq = tick ? p.tick->n_long : p.num_queries;

@@ -81,6 +81,7 @@ std::string plan_layout(const int64_t* offsets, int64_t num_seqs, int32_t long_c
     out.num_groups = (n_short + kGroup - 1) / kGroup;
     out.group_off.resize(static_cast<size_t>(out.num_groups));
     out.group_len.resize(static_cast<size_t>(out.num_groups));
+    out.group_res.assign(static_cast<size_t>(out.num_groups), 0);
     out.perm.assign(static_cast<size_t>(out.num_groups * kGroup), -1);
     int64_t off = 0;
     for (int64_t g = 0; g < out.num_groups; ++g) {
@@ -91,6 +92,7 @@ std::string plan_layout(const int64_t* offsets, int64_t num_seqs, int32_t long_c
             out.perm[static_cast<size_t>(s)] = id;
             glen = std::max(glen, offsets[id + 1] - offsets[id]);
             out.short_residues += offsets[id + 1] - offsets[id];
+            out.group_res[static_cast<size_t>(g)] += offsets[id + 1] - offsets[id];
         }
         glen = (glen + 7) / 8 * 8;
         out.group_len[static_cast<size_t>(g)] = static_cast<int32_t>(glen);

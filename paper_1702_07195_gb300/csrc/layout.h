@@ -20,6 +20,7 @@ struct Layout {
     int64_t short_residues = 0;  // residues covered by the interleaved groups
     std::vector<int64_t> group_off;
     std::vector<int32_t> group_len;
+    std::vector<int64_t> group_res;   // real residues per group
     std::vector<int32_t> perm;      // num_groups * 64, -1 for fillers
     std::vector<int32_t> long_ids;  // longest first
 };

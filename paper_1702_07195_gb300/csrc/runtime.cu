@@ -56,6 +56,11 @@ bool graphs_enabled() {
     return !(v && v[0] == '0');
 }
 
+int64_t forced_split() {
+    const char* v = std::getenv("SWGB_GROUP_SPLIT");
+    return v ? std::atoll(v) : -1;
+}
+
 bool mq_enabled() {
     const char* v = std::getenv("SWGB_MQ");
     return !(v && v[0] == '0');
@@ -208,6 +213,56 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         P.rows_pad = round_up(static_cast<int64_t>(P.num_steps) * mqT, kQpRows);
     }
 
+    // Groups whose single-warp work would outlast the rest of the search run on the int32
+    // intra-task kernel instead (one warp per pair): pick the split that minimises
+    // max(inter work / rate, longest inter item) + routed work / intra rate.
+    {
+        const double scale = db->sms / 152.0;
+        const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale, r_intra = 2.4e12 * scale;
+        const int64_t warps = static_cast<int64_t>(db->sms) *
+                              std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]) * W;
+        double sum_m = 0, max_m = 0;
+        for (int q = 0; q < nq; ++q) {
+            sum_m += P.m[static_cast<size_t>(q)];
+            max_m = std::max<double>(max_m, P.m[static_cast<size_t>(q)]);
+        }
+        const double per_item_rows = P.mq ? sum_m * 32.0 : max_m * 64.0;
+        int64_t best_s = G;
+        if (P.int16_ok && G > 0) {
+            std::vector<double> pre(static_cast<size_t>(G) + 1, 0.0);
+            for (int64_t g = 0; g < G; ++g)
+                pre[static_cast<size_t>(g) + 1] = pre[static_cast<size_t>(g)] + db->layout.group_res[static_cast<size_t>(g)];
+            double best_t = 1e300;
+            for (int64_t s = G; s >= 0; --s) {
+                const double w_in = sum_m * pre[static_cast<size_t>(s)];
+                const double w_out = sum_m * (pre[static_cast<size_t>(G)] - pre[static_cast<size_t>(s)]);
+                const double crit = s > 0 ? per_item_rows * db->layout.group_len[static_cast<size_t>(s - 1)] * warps / r_inter : 0.0;
+                const double t = std::max(w_in / r_inter, crit) + w_out / r_intra;
+                if (t < best_t * 0.999) {
+                    best_t = t;
+                    best_s = s;
+                }
+            }
+        }
+        const int64_t f = forced_split();
+        if (f >= 0) best_s = std::min<int64_t>(f, G);
+        if (db->no_route) best_s = G;
+        P.g_split = best_s;
+    }
+    if (P.g_split < G && !items.empty()) {   // drop the routed groups from the inter items
+        std::vector<InterItem> kept;
+        kept.reserve(items.size());
+        for (const InterItem& it : items) {
+            if (it.group >= P.g_split) continue;
+            InterItem k2 = it;
+            k2.ngroups = static_cast<int32_t>(std::min<int64_t>(it.ngroups, P.g_split - it.group));
+            kept.push_back(k2);
+        }
+        items.swap(kept);
+        P.num_items = static_cast<int64_t>(items.size());
+    }
+    if (P.g_split == 0) P.mq = false;
+
     // Scratch shared by all plans of this database.
     P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]);
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
@@ -281,7 +336,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         mp.rows_pad = P.rows_pad;
         mp.steps = P.steps.ptr;
         mp.num_steps = P.num_steps;
-        mp.num_half_groups = static_cast<int32_t>(2 * G);
+        mp.num_half_groups = static_cast<int32_t>(2 * P.g_split);
         mp.alphabet1 = A + 1;
         mp.ctrl = db->ctrl.ptr;
         mp.flags = db->flags.ptr;
@@ -290,6 +345,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         mp.bnd = db->bnd.ptr;
         mp.bnd_stride = bnd_stride;
         mp.gaps = gaps;
+        mp.tick = nullptr;
     }
     IntraParams& jp = P.intra;
     jp.plain = db->plain.ptr;
@@ -308,11 +364,17 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     jp.spill_stride = spill_stride;
     jp.gaps = gaps;
     jp.qp_add = goe - P.qp_bias;
+    jp.perm = db->perm.ptr;
+    jp.slot_begin = P.g_split * kGroupSeqs;
+    jp.slot_end = G * kGroupSeqs;
 
     for (int q = 0; q < nq; ++q) {
         P.cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * db->num_residues;
-        if (P.int16_ok)
-            P.inter_cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * db->layout.short_residues;
+        if (P.int16_ok) {
+            int64_t res_in = 0;
+            for (int64_t g = 0; g < P.g_split; ++g) res_in += db->layout.group_res[static_cast<size_t>(g)];
+            P.inter_cells += static_cast<int64_t>(P.m[static_cast<size_t>(q)]) * res_in;
+        }
     }
     if (db->plans.size() >= 32) {
         if (db->done_recorded) cudaEventSynchronize(db->ev[4]);   // its graph may still run
@@ -348,7 +410,7 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     ++launches;
     CU(record(db->ev[1], st));
     if (P.mq) {
-        CU(launch_build_pp(d_queries, P.qoff.ptr, P.steps.ptr, P.num_steps,
+        CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.steps.ptr, P.num_steps, nullptr,
                            inter_mq_variant_rows(P.variant), P.matrix.ptr, db->A, P.qp_bias,
                            P.pp.ptr, P.rows_pad, db->ctrl.ptr, st));
         CU(launch_inter_mq(P.inter_mq, P.variant, P.inter_grid, st));
@@ -365,13 +427,20 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
             CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
-    } else if (jp.num_long > 0) {
-        jp.mode = kIntraLong;
-        CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
-        ++launches;
+    } else {
+        if (jp.num_long > 0) {
+            jp.mode = kIntraLong;
+            CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            ++launches;
+        }
+        if (P.g_split < db->layout.num_groups) {
+            jp.mode = kIntraGroups;
+            CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            ++launches;
+        }
     }
     CU(record(db->ev[3], st));
-    if (P.int16_ok && P.num_items > 0) {
+    if (P.int16_ok && (P.num_items > 0 || P.mq)) {
         jp.mode = kIntraRescore;
         CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
         ++launches;
@@ -416,6 +485,8 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(gap_extend);
     key.push_back(db->variant);
     key.push_back(mq_enabled() ? 1 : 0);
+    key.push_back(forced_split());
+    key.push_back(db->no_route ? 1 : 0);
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 

@@ -74,6 +74,7 @@ struct Plan {
     DevBuf<int8_t> matrix;
     InterParams inter{};
     IntraParams intra{};
+    int64_t g_split = 0;      // groups [g_split, G) run on the int32 kernel (critical path)
     // multi-query kernel (two queries per register against one subject)
     bool mq = false;
     int32_t num_steps = 0;
@@ -117,6 +118,7 @@ struct sw_db {
     std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 32
     // kernel choice
     int variant = 0;
+    bool no_route = false;    // set by the autotuner: every group stays on the inter-task kernel
     int inter_occ[swgb::kMaxVariants] = {};
     int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;

@@ -33,7 +33,7 @@ struct Request {
     std::vector<uint8_t> query;
     int32_t m = 0;
     int slot = -1;
-    int64_t chunks_left = 0;   // chunks [0, chunks_left) still to run, highest first
+    int32_t slices_left = 0;   // database slices still to scan (one per tick, cyclically)
     bool long_pending = false;
     int64_t state_bytes = 0;
     double t_submit = 0, t_done = 0;
@@ -49,9 +49,13 @@ struct sw_server {
     std::vector<int8_t> matrix;
     int32_t goe = 0, ge = 0, max_s = 0;
     sw_server_options opt{};
-    int variant = 0, W = 4;
-    int64_t nchunks = 0, chunks_per_share = 1, target_items = 1;
-    int inter_grid = 0, intra_grid = 0;
+    int variant = 0, W = 4, T = 64;
+    int64_t nchunks = 0;
+    std::vector<int64_t> slice_chunk;   // slice k = chunks [slice_chunk[k], slice_chunk[k+1])
+    int32_t cur_slice = 0;
+    int inter_grid = 0, intra_grid = 0, mq_grid = 0;
+    bool mq_ok = false;
+    int64_t max_steps = 0, rows_pad = 0;
     int64_t N = 0, mpad_max = 0;
     // device
     DevBuf<uint8_t> q_buf;
@@ -63,13 +67,19 @@ struct sw_server {
     DevBuf<int32_t> mpad;
     DevBuf<int8_t> dmat;
     DevBuf<TickDesc> tick_d;
+    DevBuf<int64_t> qstart;           // per slot: start of its query in q_buf
+    DevBuf<int32_t> qlen;             // per slot: query length
+    DevBuf<MqStep> steps_d;
+    DevBuf<uint32_t> pp;
+    MqStep* steps_h = nullptr;        // pinned
     DevBuf<Control> ctrl;
     DevBuf<FlagEntry> flags;
     DevBuf<uint4> bnd;
     DevBuf<int2> spill;
     TickDesc* tick_h = nullptr;       // pinned
     cudaStream_t st = nullptr, cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;      // one request in flight: two subjects per register
+    cudaGraphExec_t graph_mq = nullptr;   // two or more: two queries per register
     cudaEvent_t ev = nullptr;
     // host state
     std::mutex mu;
@@ -85,6 +95,7 @@ struct sw_server {
     // stats
     std::vector<double> latencies;
     int64_t submitted = 0, completed = 0, rejected = 0, ticks = 0, joined = 0, cells = 0;
+    int64_t mq_ticks = 0;
     int32_t max_in_flight = 0;
     double t_first = 0, t_last = 0;
 };
@@ -122,6 +133,8 @@ sw_status start_request(sw_server* s, Request* r) {
     SCU(cudaMemcpyAsync(s->descs.ptr + slot, &d, sizeof(d), cudaMemcpyHostToDevice, s->st));
     SCU(cudaMemcpyAsync(s->qoff.ptr + 2 * slot, qo, sizeof(qo), cudaMemcpyHostToDevice, s->st));
     SCU(cudaMemcpyAsync(s->mpad.ptr + slot, &mpv, sizeof(mpv), cudaMemcpyHostToDevice, s->st));
+    const int32_t len = r->m;
+    SCU(cudaMemcpyAsync(s->qlen.ptr + slot, &len, sizeof(len), cudaMemcpyHostToDevice, s->st));
     SCU(launch_build_qp(dq, s->qoff.ptr + 2 * slot, 1, s->dmat.ptr, s->A, s->goe, s->qp_off.ptr,
                         s->mpad.ptr + slot, const_cast<int16_t*>(d.qp), mp, s->ctrl.ptr, s->st));
     add_launches(1);
@@ -130,8 +143,9 @@ sw_status start_request(sw_server* s, Request* r) {
     return SW_OK;
 }
 
-sw_status capture_tick_graph(sw_server* s, const DbView& v) {
+sw_status capture_tick_graphs(sw_server* s, const DbView& v) {
     const Gaps gaps{s->goe, s->ge, std::min(s->goe, s->ge)};
+    const int64_t bnd_stride = std::max<int64_t>(1, v.max_group_len / 2 * kWarp);
     InterParams ip{};
     ip.inter = v.inter;
     ip.group_off = v.group_off;
@@ -146,10 +160,30 @@ sw_status capture_tick_graph(sw_server* s, const DbView& v) {
     ip.flag_cap = static_cast<uint32_t>(s->flags.cap);
     ip.thresh = 32767 - std::max(0, s->max_s);
     ip.bnd = s->bnd.ptr;
-    ip.bnd_stride = std::max<int64_t>(1, v.max_group_len / 2 * kWarp);
+    ip.bnd_stride = bnd_stride;
     ip.gaps = gaps;
     ip.tick = s->tick_d.ptr;
     ip.num_groups = static_cast<int32_t>(v.num_groups);
+    InterMqParams mp{};
+    mp.inter = v.inter;
+    mp.group_off = v.group_off;
+    mp.group_len = v.group_len;
+    mp.perm = v.perm;
+    mp.queries = s->descs.ptr;
+    mp.pp = s->pp.ptr;
+    mp.rows_pad = s->rows_pad;
+    mp.steps = s->steps_d.ptr;
+    mp.num_steps = 0;
+    mp.num_half_groups = 0;
+    mp.alphabet1 = s->A + 1;
+    mp.ctrl = s->ctrl.ptr;
+    mp.flags = s->flags.ptr;
+    mp.flag_cap = static_cast<uint32_t>(s->flags.cap);
+    mp.thresh = ip.thresh;
+    mp.bnd = s->bnd.ptr;
+    mp.bnd_stride = bnd_stride;
+    mp.gaps = gaps;
+    mp.tick = s->tick_d.ptr;
     IntraParams jp{};
     jp.plain = v.plain;
     jp.plain_off = v.plain_off;
@@ -168,28 +202,42 @@ sw_status capture_tick_graph(sw_server* s, const DbView& v) {
     jp.gaps = gaps;
     jp.qp_add = 0;
     jp.tick = s->tick_d.ptr;
-    cudaGraph_t g = nullptr;
-    SCU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemcpyAsync(s->tick_d.ptr, s->tick_h, sizeof(TickDesc), cudaMemcpyHostToDevice, s->cap);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->ctrl.ptr, 0, sizeof(Control), s->cap);
-    if (e == cudaSuccess && v.num_groups > 0) e = launch_inter(ip, s->variant, s->inter_grid, s->cap);
-    if (e == cudaSuccess && v.num_long > 0) {
-        jp.mode = kIntraTickLong;
-        e = launch_intra(jp, s->intra_grid, intra_block_threads(), s->cap);
+    for (int mode = 0; mode < (s->mq_ok ? 2 : 1); ++mode) {
+        cudaGraph_t g = nullptr;
+        SCU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(s->tick_d.ptr, s->tick_h, sizeof(TickDesc),
+                                        cudaMemcpyHostToDevice, s->cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->ctrl.ptr, 0, sizeof(Control), s->cap);
+        if (mode == 1) {
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->steps_d.ptr, s->steps_h, sizeof(MqStep) * s->max_steps,
+                                    cudaMemcpyHostToDevice, s->cap);
+            if (e == cudaSuccess)
+                e = launch_build_pp(s->q_buf.ptr, s->qstart.ptr, s->qlen.ptr, s->steps_d.ptr, 0,
+                                    s->tick_d.ptr, s->T, s->dmat.ptr, s->A, s->goe, s->pp.ptr,
+                                    s->rows_pad, s->ctrl.ptr, s->cap);
+            if (e == cudaSuccess && v.num_groups > 0) e = launch_inter_mq(mp, s->variant, s->mq_grid, s->cap);
+        } else if (e == cudaSuccess && v.num_groups > 0) {
+            e = launch_inter(ip, s->variant, s->inter_grid, s->cap);
+        }
+        if (e == cudaSuccess && v.num_long > 0) {
+            jp.mode = kIntraTickLong;
+            e = launch_intra(jp, s->intra_grid, intra_block_threads(), s->cap);
+        }
+        if (e == cudaSuccess && v.num_groups > 0) {
+            jp.mode = kIntraRescore;
+            e = launch_intra(jp, s->intra_grid, intra_block_threads(), s->cap);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cerr(e, "tick capture");
+        }
+        if (e2 != cudaSuccess) return cerr(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(mode == 1 ? &s->graph_mq : &s->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cerr(e, "cudaGraphInstantiate");
     }
-    if (e == cudaSuccess && v.num_groups > 0) {
-        jp.mode = kIntraRescore;
-        e = launch_intra(jp, s->intra_grid, intra_block_threads(), s->cap);
-    }
-    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
-    if (e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return cerr(e, "tick capture");
-    }
-    if (e2 != cudaSuccess) return cerr(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&s->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cerr(e, "cudaGraphInstantiate");
     return SW_OK;
 }
 
@@ -207,11 +255,72 @@ void finish(sw_server* s, Request* r) {
     ++s->completed;
 }
 
+// Fills the host tick descriptor (and, with two or more requests, the two query streams)
+// for database slice `c`.  Returns true for a multi-query tick.
+bool build_tick(sw_server* s, int32_t c, const std::vector<Request*>& act) {
+    TickDesc& t = *s->tick_h;
+    t.n = 0;
+    t.n_long = 0;
+    t.prefix[0] = 0;
+    for (Request* r : act)
+        if (r->long_pending) t.long_slot[t.n_long++] = r->slot;
+    const int64_t c0 = s->slice_chunk[static_cast<size_t>(c)], c1 = s->slice_chunk[static_cast<size_t>(c) + 1];
+    const bool mq = s->mq_ok && act.size() >= 2;
+    if (!mq) {
+        for (Request* r : act) {   // one request: its chunks of the slice, longest first
+            t.slot[t.n] = r->slot;
+            t.chunk_end[t.n] = static_cast<int32_t>(c1);
+            t.prefix[t.n + 1] = t.prefix[t.n] + static_cast<int32_t>(c1 - c0);
+            ++t.n;
+        }
+        t.mq_steps = 0;
+        return false;
+    }
+    // Two streams of T-row strips, balanced by strip count, longest query first.
+    std::vector<Request*> order(act.begin(), act.end());
+    std::stable_sort(order.begin(), order.end(), [](Request* a, Request* b) { return a->m > b->m; });
+    std::vector<Request*> stream[2];
+    int64_t len[2] = {0, 0};
+    for (Request* r : order) {
+        const int x = len[0] <= len[1] ? 0 : 1;
+        stream[x].push_back(r);
+        len[x] += (r->m + s->T - 1) / s->T;
+    }
+    const int64_t n = std::max(len[0], len[1]);
+    for (int64_t k = 0; k < n; ++k) s->steps_h[k] = MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0};
+    for (int x = 0; x < 2; ++x) {
+        int64_t k = 0;
+        for (Request* r : stream[x]) {
+            const int32_t S = (r->m + s->T - 1) / s->T;
+            for (int32_t si = 0; si < S; ++si, ++k) {
+                MqStep& st = s->steps_h[k];
+                uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
+                if (si == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
+                if (si == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
+                st.flags = fl;
+                if (x == 0) {
+                    st.qa = r->slot;
+                    st.sa = si;
+                } else {
+                    st.qb = r->slot;
+                    st.sb = si;
+                }
+            }
+        }
+    }
+    const int64_t g0 = c0 * s->W, g1 = std::min<int64_t>(c1 * s->W, s->db->layout.num_groups);
+    t.mq_steps = static_cast<int32_t>(n);
+    t.hg_begin = static_cast<int32_t>(2 * g0);
+    t.hg_end = static_cast<int32_t>(2 * g1);
+    return true;
+}
+
 void worker_loop(sw_server* s) {
     cudaSetDevice(s->db->device);
     DbView v;
     db_view(s->db, &v);
     const int64_t num_long = v.num_long;
+    const int32_t K = static_cast<int32_t>(s->slice_chunk.size()) - 1;
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         // Admission: free slot and DP-state budget.
@@ -229,15 +338,17 @@ void worker_loop(sw_server* s) {
             s->pending.pop_front();
             if (in_flight(s) > 0) ++s->joined;
             r->slot = slot;
-            r->chunks_left = s->nchunks;
+            r->slices_left = K;
             r->long_pending = num_long > 0;
             s->active[slot] = r;
             s->state_used += r->state_bytes;
             admitted.push_back(r);
         }
-        const int n_act = in_flight(s);
-        s->max_in_flight = std::max(s->max_in_flight, n_act);
-        if (n_act == 0) {
+        std::vector<Request*> act;
+        for (Request* r : s->active)
+            if (r) act.push_back(r);
+        s->max_in_flight = std::max<int32_t>(s->max_in_flight, static_cast<int32_t>(act.size()));
+        if (act.empty()) {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
             continue;
         }
@@ -250,31 +361,28 @@ void worker_loop(sw_server* s) {
             }
         }
         if (s->stop) break;
-        // Tick: every in-flight request takes its next share of chunks.
-        TickDesc& t = *s->tick_h;
-        t.n = 0;
-        t.n_long = 0;
-        t.prefix[0] = 0;
-        std::vector<std::pair<Request*, int64_t>> took;
-        const int64_t per_req = std::max<int64_t>(s->chunks_per_share, (s->target_items + n_act - 1) / n_act);
-        for (int i = 0; i < s->opt.max_inflight; ++i) {
-            Request* r = s->active[i];
-            if (!r) continue;
-            if (r->long_pending) t.long_slot[t.n_long++] = r->slot;
-            const int64_t take = std::min(r->chunks_left, per_req);
-            if (take > 0) {
-                t.slot[t.n] = r->slot;
-                t.chunk_end[t.n] = static_cast<int32_t>(r->chunks_left);
-                t.prefix[t.n + 1] = t.prefix[t.n] + static_cast<int32_t>(take);
-                ++t.n;
-            }
-            took.emplace_back(r, take);
+        // Tick: every in-flight request scans the current database slice.
+        const int32_t c = s->cur_slice;
+        bool mq = false;
+        if (K > 0) {
+            mq = build_tick(s, c, act);
+        } else {   // no interleaved groups: only long subjects
+            TickDesc& t = *s->tick_h;
+            t.n = 0;
+            t.n_long = 0;
+            t.prefix[0] = 0;
+            t.mq_steps = 0;
+            for (Request* r : act)
+                if (r->long_pending) t.long_slot[t.n_long++] = r->slot;
         }
         lk.unlock();
-        cudaError_t e = cudaGraphLaunch(s->graph, s->st);
-        if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(s->ev);
-        add_launches(1 + (num_long > 0 ? 1 : 0) + (v.num_groups > 0 ? 1 : 0));
+        cudaError_t e = cudaSuccess;
+        if (K > 0 || num_long > 0) {
+            e = cudaGraphLaunch(mq ? s->graph_mq : s->graph, s->st);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(s->ev);
+            add_launches(mq ? 5 : 3);
+        }
         lk.lock();
         if (e != cudaSuccess) {
             s->worker_status = cerr(e, "tick");
@@ -282,11 +390,12 @@ void worker_loop(sw_server* s) {
             break;
         }
         ++s->ticks;
-        for (auto& tr : took) {
-            Request* r = tr.first;
-            r->chunks_left -= tr.second;
+        s->mq_ticks += mq ? 1 : 0;
+        if (K > 0) s->cur_slice = (c + 1) % K;
+        for (Request* r : act) {
+            r->slices_left -= 1;
             r->long_pending = false;
-            if (r->chunks_left == 0) {
+            if (r->slices_left <= 0) {
                 r->result.resize(static_cast<size_t>(s->N));
                 e = cudaMemcpy(r->result.data(), s->scores.ptr + static_cast<int64_t>(r->slot) * s->N,
                                sizeof(int32_t) * s->N, cudaMemcpyDeviceToHost);
@@ -351,12 +460,35 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     s->N = v.num_seqs;
     s->variant = db->variant;
     s->W = inter_variant_warps(s->variant);
+    s->T = inter_mq_variant_rows(s->variant);
     s->nchunks = (v.num_groups + s->W - 1) / s->W;
-    s->chunks_per_share = std::max<int64_t>(1, (s->nchunks + s->opt.slices - 1) / s->opt.slices);
+    // Slices of about equal residue work, whole chunks of W groups each.
+    {
+        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(s->opt.slices, s->nchunks));
+        std::vector<int64_t> cres(static_cast<size_t>(s->nchunks) + 1, 0);
+        for (int64_t c = 0; c < s->nchunks; ++c) {
+            int64_t r = 0;
+            for (int64_t g = c * s->W; g < std::min<int64_t>((c + 1) * s->W, v.num_groups); ++g)
+                r += db->layout.group_res[static_cast<size_t>(g)];
+            cres[static_cast<size_t>(c) + 1] = cres[static_cast<size_t>(c)] + r;
+        }
+        s->slice_chunk.assign(1, 0);
+        for (int64_t k = 1; k < K; ++k) {
+            const int64_t target = cres.back() * k / K;
+            int64_t c = s->slice_chunk.back() + 1;
+            while (c < s->nchunks && cres[static_cast<size_t>(c)] < target) ++c;
+            if (c < s->nchunks) s->slice_chunk.push_back(c);
+        }
+        if (s->nchunks > 0) s->slice_chunk.push_back(s->nchunks);
+    }
     s->inter_grid = v.sms * std::max(1, db->inter_occ[s->variant]);
+    s->mq_grid = v.sms * std::max(1, db->inter_mq_occ[s->variant]);
+    s->mq_ok = db->inter_mq_occ[s->variant] > 0 && v.num_groups > 0;
     s->intra_grid = v.sms * std::max(1, v.intra_occ);
-    s->target_items = 2 * static_cast<int64_t>(s->inter_grid);
     s->mpad_max = (s->opt.max_query_len + kQpRows - 1) / kQpRows * kQpRows;
+    s->max_steps = std::max<int64_t>(1, static_cast<int64_t>(s->opt.max_inflight) *
+                                            ((s->opt.max_query_len + s->T - 1) / s->T));
+    s->rows_pad = (s->max_steps * s->T + kQpRows - 1) / kQpRows * kQpRows;
     const int S = s->opt.max_inflight;
     SCU(s->q_buf.ensure(static_cast<size_t>(S) * s->opt.max_query_len));
     SCU(s->qp_buf.ensure(static_cast<size_t>(S) * (s->A + 1) * s->mpad_max));
@@ -377,11 +509,26 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     SCU(s->dmat.ensure(s->matrix.size()));
     SCU(cudaMemcpy(s->dmat.ptr, s->matrix.data(), s->matrix.size(), cudaMemcpyHostToDevice));
     SCU(s->tick_d.ensure(1));
+    SCU(s->qstart.ensure(static_cast<size_t>(S)));
+    SCU(s->qlen.ensure(static_cast<size_t>(S)));
+    {
+        std::vector<int64_t> st0(static_cast<size_t>(S));
+        for (int i = 0; i < S; ++i) st0[static_cast<size_t>(i)] = static_cast<int64_t>(i) * s->opt.max_query_len;
+        SCU(cudaMemcpy(s->qstart.ptr, st0.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice));
+        SCU(cudaMemset(s->qlen.ptr, 0, sizeof(int32_t) * S));
+    }
+    if (s->mq_ok) {
+        SCU(s->steps_d.ensure(static_cast<size_t>(s->max_steps)));
+        SCU(s->pp.ensure(static_cast<size_t>((s->A + 1) * s->rows_pad)));
+        SCU(cudaMallocHost(reinterpret_cast<void**>(&s->steps_h), sizeof(MqStep) * s->max_steps));
+        std::memset(s->steps_h, 0, sizeof(MqStep) * s->max_steps);
+    }
     SCU(s->ctrl.ensure(1));
     SCU(s->flags.ensure(static_cast<size_t>(std::min<int64_t>(std::max<int64_t>(s->N * S, 1), 1 << 20))));
     const int64_t bnd_stride = std::max<int64_t>(1, v.max_group_len / 2 * kWarp);
     const int64_t spill_stride = std::max<int64_t>(1, (v.max_len + 31) / 32 * 32 + 64);
-    SCU(s->bnd.ensure(static_cast<size_t>(static_cast<int64_t>(s->inter_grid) * s->W * bnd_stride)));
+    SCU(s->bnd.ensure(static_cast<size_t>(static_cast<int64_t>(std::max(s->inter_grid, s->mq_grid)) *
+                                          s->W * bnd_stride)));
     SCU(s->spill.ensure(static_cast<size_t>(static_cast<int64_t>(s->intra_grid) *
                                             (intra_block_threads() / kWarp) * spill_stride)));
     SCU(cudaMallocHost(reinterpret_cast<void**>(&s->tick_h), sizeof(TickDesc)));
@@ -389,7 +536,7 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     SCU(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
     SCU(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
     SCU(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
-    sw_status st = capture_tick_graph(s.get(), v);
+    sw_status st = capture_tick_graphs(s.get(), v);
     if (st != SW_OK) return st;
     s->active.assign(static_cast<size_t>(S), nullptr);
     sw_server* raw = s.get();
@@ -512,6 +659,8 @@ void sw_server_destroy(sw_server* s) {
         DeviceGuard guard(s->db->device);
         if (s->st) cudaStreamSynchronize(s->st);
         if (s->graph) cudaGraphExecDestroy(s->graph);
+        if (s->graph_mq) cudaGraphExecDestroy(s->graph_mq);
+        if (s->steps_h) cudaFreeHost(s->steps_h);
         if (s->ev) cudaEventDestroy(s->ev);
         if (s->st) cudaStreamDestroy(s->st);
         if (s->cap) cudaStreamDestroy(s->cap);
@@ -525,6 +674,10 @@ void sw_server_destroy(sw_server* s) {
         s->mpad.release();
         s->dmat.release();
         s->tick_d.release();
+        s->qstart.release();
+        s->qlen.release();
+        s->steps_d.release();
+        s->pp.release();
         s->ctrl.release();
         s->flags.release();
         s->bnd.release();

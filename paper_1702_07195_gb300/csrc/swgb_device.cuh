@@ -46,6 +46,8 @@ constexpr int kTickMax = 128;
 struct TickDesc {
     int32_t n;                        // requests in this tick
     int32_t n_long;                   // requests whose long subjects run in this tick
+    int32_t mq_steps;                 // multi-query ticks: strip pairs of the two streams
+    int32_t hg_begin, hg_end;         // multi-query ticks: half-groups of the database slice
     int32_t slot[kTickMax];           // query slot of request s
     int32_t chunk_end[kTickMax];      // its chunks [chunk_end - count, chunk_end), longest first
     int32_t prefix[kTickMax + 1];     // item offsets: request s owns items [prefix[s], prefix[s+1])
@@ -59,7 +61,8 @@ struct FlagEntry {
 
 // Zeroed before every launch sequence.
 struct Control {
-    unsigned long long next_intra;   // intra-task pair counter
+    unsigned long long next_intra;   // intra-task pair counter (long subjects, all pairs)
+    unsigned long long next_groups;  // intra-task pair counter (routed groups)
     unsigned long long sweep_next;   // rescore sweep block counter
     unsigned int next_inter;         // inter-task item counter
     unsigned int next_rescore;       // saturation-list counter
@@ -123,6 +126,7 @@ struct InterMqParams {
     uint4* bnd;
     int64_t bnd_stride;
     Gaps gaps;
+    const TickDesc* tick;       // non-null: num_steps and the half-group range come from here
 };
 
 // Work source of the int32 intra-task kernel.
@@ -130,7 +134,8 @@ enum IntraMode : int32_t {
     kIntraLong = 0,      // (query, long subject) pairs: num_queries x num_long
     kIntraRescore = 1,   // entries of the saturation list, then a sweep if it overflowed
     kIntraAll = 2,       // every (query, sequence) pair (int16 path not applicable)
-    kIntraTickLong = 3   // serving: long subjects of the requests admitted in this tick
+    kIntraTickLong = 3,  // serving: long subjects of the requests admitted in this tick
+    kIntraGroups = 4     // group slots [slot_begin, slot_end) of the layout, every query
 };
 
 struct IntraParams {
@@ -152,6 +157,8 @@ struct IntraParams {
     Gaps gaps;
     int32_t qp_add;             // Goe minus the profile's bias (0 unless Goe is too large)
     const TickDesc* tick;       // kIntraTickLong
+    const int32_t* perm;        // kIntraGroups: group slot -> sequence id (-1 filler)
+    int64_t slot_begin, slot_end;
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -172,10 +179,13 @@ int inter_mq_variant_warps(int variant);
 size_t inter_mq_smem_bytes(int alphabet1);
 int inter_mq_occupancy(int variant, int alphabet1);
 cudaError_t launch_inter_mq(const InterMqParams& p, int variant, int grid, cudaStream_t st);
-cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, const MqStep* d_steps,
-                            int32_t num_steps, int32_t rows_per_strip, const int8_t* d_matrix,
-                            int32_t A, int32_t bias, uint32_t* d_pp, int64_t rows_pad,
-                            Control* ctrl, cudaStream_t st);
+// Query q's residues start at d_queries[d_qoff[q]]; its length is d_qlen[q] when d_qlen is
+// given, else d_qoff[q + 1] - d_qoff[q].  With `tick`, the step count comes from the device.
+cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, const int32_t* d_qlen,
+                            const MqStep* d_steps, int32_t num_steps, const TickDesc* tick,
+                            int32_t rows_per_strip, const int8_t* d_matrix, int32_t A,
+                            int32_t bias, uint32_t* d_pp, int64_t rows_pad, Control* ctrl,
+                            cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
 int intra_block_threads();
 int intra_rows_per_pass();

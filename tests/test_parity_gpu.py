@@ -117,10 +117,11 @@ def test_empty_database(sw):
 
 
 @pytest.mark.parametrize("flag_cap", [0, 2, 1])
-def test_saturating_hits_rescored_exactly(sw, flag_cap):
-    """Planted hits above the int16 range go through the inter-task kernel (cutoff 8192),
-    are flagged and rescored in int32; flag_cap 1 and 2 overflow the saturation list and
-    exercise the sweep over all scores."""
+def test_saturating_hits_rescored_exactly(sw, flag_cap, monkeypatch):
+    """Planted hits above the int16 range go through the inter-task kernel (cutoff 8192, no
+    routing of long groups), are flagged and rescored in int32; flag_cap 1 and 2 overflow the
+    saturation list and exercise the sweep over all scores."""
+    monkeypatch.setenv("SWGB_GROUP_SPLIT", "1000000000")
     wl = w.plain(seed=2, scale=0.05)
     db2, q2, idx = w.plant_saturating(wl.db, wl.queries[0], count=6, run=3200)
     with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, long_cutoff=8192,
@@ -263,6 +264,7 @@ def test_multi_query_kernel_matches_oracle(sw, variant, monkeypatch):
     """Two queries per register (multi-query kernel): ragged query lengths around the strip
     height, an empty query in the batch, an odd count, and planted int16 saturation, for every
     variant; the same batch with the multi-query path switched off agrees."""
+    monkeypatch.setenv("SWGB_GROUP_SPLIT", "1000000000")   # keep every group on the int16 path
     rng = np.random.default_rng(100 + variant)
     base = w.batched(seed=14, scale=0.003).db
     db2, q_sat, _ = w.plant_saturating(base, w.draw_residues(rng, 20), count=3, run=3100)
@@ -280,3 +282,60 @@ def test_multi_query_kernel_matches_oracle(sw, variant, monkeypatch):
         got2 = sw.sw_search_batch(h, qs, sm, 10, 2)
         assert sw.sw_get_stats(h)["multi_query"] == 0
     _check(got2, exp, "single-query kernel")
+
+
+@pytest.mark.parametrize("split", ["0", "1", "3", "auto"])
+def test_group_routing_to_intra_kernel(sw, split, monkeypatch):
+    """Groups above the split run on the int32 intra-task kernel (one warp per pair); the
+    scores do not depend on where the split falls (single- and multi-query batches)."""
+    if split != "auto":
+        monkeypatch.setenv("SWGB_GROUP_SPLIT", split)
+    wl = w.plain(seed=31, scale=0.03)                # ~300 sequences = 5 groups
+    rng = np.random.default_rng(7)
+    qs1 = [wl.queries[0]]
+    qs2 = [wl.queries[0], w.draw_residues(rng, 77), w.draw_residues(rng, 300)]
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        got1 = sw.sw_search_batch(h, qs1, wl.matrix, 10, 2)
+        st1 = sw.sw_get_stats(h)
+        got2 = sw.sw_search_batch(h, qs2, wl.matrix, 10, 2)
+    _check(got1, _oracle_all(qs1, wl.db, wl.matrix, 10, 2), f"split {split} single")
+    _check(got2, _oracle_all(qs2, wl.db, wl.matrix, 10, 2), f"split {split} multi")
+    if split in ("0", "auto"):
+        assert st1["intra_ms"] > 0      # a small database routes its long groups
+
+
+@pytest.mark.parametrize("k", [1, 5, 64, 1000, 4096])
+def test_sorting_stage_topk(sw, k):
+    """Sorting stage: device top-k equals a full sort by (descending score, ascending index)
+    of the oracle's scores; heavy ties (random small scores) and large scores (> 2^16, so the
+    radix select runs over several digits) included."""
+    import torch
+    rng = np.random.default_rng(k)
+    n = 9000
+    rows = [rng.integers(0, 40, size=n), rng.integers(0, 3_000_000, size=n),
+            np.zeros(n, np.int64), np.concatenate([np.full(n - 3, 7), [70000, 70000, 9]])]
+    sc = np.stack(rows).astype(np.int32)
+    d = torch.from_numpy(sc.reshape(-1)).cuda()
+    top_s, top_i = sw.sw_topk(d, n, sc.shape[0], k)
+    torch.cuda.synchronize()
+    for q in range(sc.shape[0]):
+        order = np.lexsort((np.arange(n), -sc[q].astype(np.int64)))[:k]
+        assert np.array_equal(top_i[q].cpu().numpy(), order), f"row {q}"
+        assert np.array_equal(top_s[q].cpu().numpy(), sc[q][order]), f"row {q}"
+
+
+def test_sorting_stage_after_search(sw):
+    """Search then sort on the device: the top hits are the oracle's best scores."""
+    import torch
+    wl = w.plain(seed=41, scale=0.1)
+    db2, q2, planted = w.plant_saturating(wl.db, wl.queries[0], count=4, run=3100)
+    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE) as h:
+        dq = torch.from_numpy(q2).cuda()
+        out = torch.empty(h.num_seqs, dtype=torch.int32, device="cuda")
+        sw.sw_search_batch_device(h, dq, np.array([0, len(q2)], np.int64), wl.matrix, 10, 2, out)
+        top_s, top_i = sw.sw_topk(out, h.num_seqs, 1, 10)
+        torch.cuda.synchronize()
+    exp = _oracle_all([q2], db2, wl.matrix, 10, 2)[0]
+    order = np.lexsort((np.arange(len(exp)), -exp))[:10]
+    assert np.array_equal(top_i[0].cpu().numpy(), order)
+    assert set(planted) <= set(order.tolist())
