@@ -297,13 +297,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     launches0 = sw.sw_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    inter_ms, flagged = [], 0
+    inter_ms, flagged, st_timed = [], 0, None
     ev0.record(stream)
     for _ in range(args.steps):
         step()
-        st = sw.sw_get_stats(db)          # per-kernel CUDA events on the launch stream
-        inter_ms.append(st["inter_ms"])
-        flagged += st["flagged"]
+        st_timed = sw.sw_get_stats(db)    # per-kernel CUDA events on the launch stream
+        inter_ms.append(st_timed["inter_ms"])
+        flagged += st_timed["flagged"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -383,7 +383,7 @@ def run_ours(args, world, rank, local):
     sms = props.multi_processor_count
     f_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_gcups = sms * LANE_OPS_PER_CLK_SM * f_max * 2.0 / OPS_PER_CELL_PAIR / 1e9
-    st_last = sw.sw_get_stats(db)
+    st_last = st_timed if st_timed is not None else sw.sw_get_stats(db)
     inter_cells = st_last["inter_cells"]
     kernel_name = "k_inter_mq_i16x2" if st_last.get("multi_query") else INTER_KERNEL
     k_ms = statistics.mean(inter_ms) if inter_ms else float("nan")
@@ -431,7 +431,9 @@ def run_serving(args, world, rank, local):
     wl = make_workload("batched", args.seed + rank, args.scale)
     db = sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE)
     R = wl.db.num_residues
-    srv = sw.Server(db, wl.matrix, wl.gap_open, wl.gap_extend, max_inflight=32, slices=8)
+    probe = w.serving_queries(2, seed=args.seed + 50)
+    tune = sw.sw_db_tune(db, probe, wl.matrix, wl.gap_open, wl.gap_extend)
+    srv = sw.Server(db, wl.matrix, wl.gap_open, wl.gap_extend, max_inflight=32, slices=0)
     # capacity: a burst of requests submitted together
     burst = w.serving_queries(48, seed=args.seed + 100)
     for t in [srv.submit(q) for q in burst[:8]]:      # warm-up
@@ -476,7 +478,8 @@ def run_serving(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (int32 rescore)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT["serving"], "db_seqs": wl.db.num_seqs,
-                       "db_residues": R, "max_inflight": 32, "slices": 8,
+                       "db_residues": R, "max_inflight": 32, "slices": "auto",
+                       "kernel_variant": tune,
                        "capacity_rps": capacity, "capacity_gcups": cap_stats["gcups"]},
             "serving": results, "clocks": clocks}
     if rank == 0:

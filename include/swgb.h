@@ -170,7 +170,8 @@ sw_status sw_topk(const int32_t *d_scores, int64_t num_seqs, int32_t num_queries
  * is cut into `slices` of about equal residue work; a background thread runs "ticks" that scan
  * the slices cyclically.  In a tick every in-flight request aligns against the current slice:
  * one replay of a captured CUDA graph, with two queries per int16x2 register when two or more
- * requests are in flight, followed by the int32 work (long subjects of newly admitted
+ * requests are in flight (split into independent batches when that is needed to keep the GPU
+ * busy), followed by the int32 work (long subjects of newly admitted
  * requests, saturated lanes).  A request admitted while others run joins at the next tick and
  * completes after one full cycle of slices; its scores (original order) are then copied to the
  * host.  Each score equals the one sw_search returns for the same query.
@@ -180,7 +181,8 @@ typedef struct {
     int32_t max_query_len;       /* longest accepted query (default 8192) */
     int64_t state_budget_bytes;  /* DP-state bytes of all in-flight requests (default 1 GiB) */
     int32_t slices;              /* database slices of the cyclic scan; a request takes one
-                                    tick per slice (default 8) */
+                                    tick per slice (default: as many as keep ~8 waves of work
+                                    items per tick, at most 16) */
     int32_t max_pending;         /* submitted but not admitted (default 4096) */
     int32_t reserved[6];
 } sw_server_options;

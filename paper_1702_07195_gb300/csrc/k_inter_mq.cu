@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
     const int num_steps = p.tick ? p.tick->mq_steps : p.num_steps;
     const int hg_begin = p.tick ? p.tick->hg_begin : 0;
     const int hg_end = p.tick ? p.tick->hg_end : p.num_half_groups;
-    const int num_items = (hg_end - hg_begin + kW - 1) / kW;
+    const int nb = p.tick ? p.tick->n_batches : 1;
+    const int n_hb = (hg_end - hg_begin + kW - 1) / kW;   // blocks of kW half-groups
+    const int num_items = n_hb * nb;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_inter, 1u));
@@ -146,16 +148,19 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
         const int it = s_item;
         __syncthreads();
         if (it >= num_items) break;
-        // longest groups first: half-groups are in ascending length order
-        const int hg = hg_begin + (num_items - 1 - it) * kW + warp;
+        // longest groups first (half-groups are in ascending length order), batches interleaved
+        const int b = it % nb;
+        const int hg = hg_begin + (n_hb - 1 - it / nb) * kW + warp;
         const bool active = hg < hg_end;
+        const int s_begin = p.tick ? p.tick->batch_step_off[b] : 0;
+        const int s_end = p.tick ? p.tick->batch_step_off[b + 1] : num_steps;
         const int g = hg >> 1, h = hg & 1;
         const int L = active ? p.group_len[g] : 0;
         const uint4* res =
             active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
         const int id = active ? p.perm[g * kGroupSeqs + 2 * lane + h] : -1;
         unsigned best = 0;
-        for (int k0 = 0; k0 < num_steps; k0 += kStepsPerChunk) {
+        for (int k0 = s_begin; k0 < s_end; k0 += kStepsPerChunk) {
             __syncthreads();
             constexpr int kVecPerRow = kChunk / 4;
             const int64_t row0 = static_cast<int64_t>(k0) * kT;
@@ -167,13 +172,13 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
             }
             __syncthreads();
             if (!active || L == 0) continue;
-            const int k_end = min(num_steps, k0 + kStepsPerChunk);
+            const int k_end = min(s_end, k0 + kStepsPerChunk);
             for (int ks = k0; ks < k_end; ++ks) {
                 const MqStep st = p.steps[ks];
                 const bool fa = st.flags & kMqFirstA, fb = st.flags & kMqFirstB;
                 const unsigned keep = (fa ? 0u : 0x0000FFFFu) | (fb ? 0u : 0xFFFF0000u);
                 strip_mq<kT>(res, L, h, bnd, s_pp + (ks - k0) * kT, pstride, keep,
-                             keep != 0u, ks + 1 < num_steps, k, best, lane);
+                             keep != 0u, ks + 1 < s_end, k, best, lane);
                 if (st.flags & kMqLastA) {
                     emit_mq(p, st.qa, id, static_cast<int>(static_cast<short>(best & 0xFFFFu)));
                     best &= 0xFFFF0000u;

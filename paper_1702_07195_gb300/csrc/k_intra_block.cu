@@ -1,0 +1,204 @@
+// Intra-task Smith-Waterman/Gotoh kernel in int32, block-shared profile variant.
+//
+// Same wavefront as k_intra_i32 (one warp per (query, subject) pair; lane l owns a strip of
+// query rows and updates column t - l at step t; rows pass between lanes by __shfl_up_sync;
+// a per-warp global buffer carries the bottom row to the next pass) but for the work sources
+// where neighbouring pairs share the query -- subjects above the inter-task cutoff and groups
+// routed off the inter-task kernel -- the four warps of a block take the same query against
+// four neighbouring subjects (longest first), so one copy of the pass's profile slice serves
+// the block.  The slice is stored as int32 (sign-extended and biased once per pass, not once
+// per cell) and each lane owns 16 rows, halving the per-step shuffles and loads per cell.
+// Eqs. sw2-sw4, Section 2; the intra-task scheme of Section 1.
+#include "swgb_device.cuh"
+
+namespace swgb {
+
+namespace {
+
+constexpr int kTB = 16;                      // query rows per lane
+constexpr int kRowsB = kTB * kWarp;          // 512 rows per pass
+constexpr int kBW = 4;                       // warps per block = subjects per block item
+constexpr int kBBlock = kBW * kWarp;
+constexpr int kPStride = kRowsB + 4;         // int32 per shared-memory profile row
+
+static_assert(kRowsB % kQpRows == 0, "profiles are padded to multiples of kQpRows");
+
+struct BlockItem {
+    int q;
+    int seq[kBW];
+};
+
+// Decodes block item `it` (longest subjects first); seq = -1 for absent / filler slots.
+__device__ bool decode_item(const IntraParams& p, unsigned long long it, BlockItem& out) {
+    if (p.mode == kIntraLong) {
+        const int64_t per_q = (p.num_long + kBW - 1) / kBW;
+        const unsigned long long total =
+            static_cast<unsigned long long>(per_q) * static_cast<unsigned long long>(p.num_queries);
+        if (it >= total) return false;
+        const int64_t c = static_cast<int64_t>(it / static_cast<unsigned long long>(p.num_queries));
+        const int qi = static_cast<int>(static_cast<int64_t>(it) - c * p.num_queries);
+        out.q = p.query_order[qi];
+        for (int w = 0; w < kBW; ++w) {
+            const int64_t li = c * kBW + w;
+            out.seq[w] = li < p.num_long ? p.long_ids[li] : -1;
+        }
+        return true;
+    }
+    // kIntraGroups: slots [slot_begin, slot_end), from the end (longest groups first)
+    const int64_t nslots = p.slot_end - p.slot_begin;
+    const int64_t per_q = (nslots + kBW - 1) / kBW;
+    const unsigned long long total =
+        static_cast<unsigned long long>(per_q) * static_cast<unsigned long long>(p.num_queries);
+    if (it >= total) return false;
+    const int64_t c = static_cast<int64_t>(it / static_cast<unsigned long long>(p.num_queries));
+    const int qi = static_cast<int>(static_cast<int64_t>(it) - c * p.num_queries);
+    out.q = p.query_order[qi];
+    for (int w = 0; w < kBW; ++w) {
+        const int64_t si = c * kBW + w;
+        out.seq[w] = si < nslots ? p.perm[p.slot_end - 1 - si] : -1;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p) {
+    extern __shared__ __align__(16) int32_t s_prof[];     // (A+1) x kPStride
+    __shared__ BlockItem s_item;
+    __shared__ int s_done;
+    __shared__ int s_passes;
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warp = threadIdx.x >> 5;
+    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kBW + warp) * p.spill_stride;
+    const int goe = p.gaps.goe, ge = p.gaps.ge, gep = p.gaps.gep;
+    unsigned long long* counter =
+        p.mode == kIntraGroups ? &p.ctrl->next_groups : &p.ctrl->next_intra;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long it = atomicAdd(counter, 1ull);
+            s_done = decode_item(p, it, s_item) ? 0 : 1;
+            if (!s_done) s_passes = (p.queries[s_item.q].m + kRowsB - 1) / kRowsB;
+        }
+        __syncthreads();
+        if (s_done) break;
+        const int q = s_item.q;
+        const QueryDesc qd = p.queries[q];
+        const int seq = s_item.seq[warp];
+        const int passes = s_passes;
+        int n = 0;
+        const uint8_t* subj = nullptr;
+        if (seq >= 0) {
+            const int64_t off = p.plain_off[seq];
+            n = static_cast<int>(p.plain_off[seq + 1] - off);
+            subj = p.plain + off;
+        }
+        int best = 0;
+        for (int pass = 0; pass < passes; ++pass) {
+            const bool first = pass == 0, last = pass == passes - 1;
+            __syncthreads();   // everyone is done with the previous slice
+            for (int v = threadIdx.x; v < p.alphabet1 * kRowsB; v += kBBlock) {
+                const int d = v / kRowsB;
+                const int r = v - d * kRowsB;
+                const int64_t row = static_cast<int64_t>(pass) * kRowsB + r;
+                // rows past the profile score 0: S' = 0 + Goe, like the profile's own padding
+                s_prof[d * kPStride + r] =
+                    row < qd.m_pad ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + row] + p.qp_add : goe;
+            }
+            __syncthreads();
+            if (n == 0 || qd.m == 0) continue;
+            int Hm[kTB], E[kTB];
+#pragma unroll
+            for (int r = 0; r < kTB; ++r) {
+                Hm[r] = -goe;
+                E[r] = -gep;
+            }
+            int hm_prev = -goe;
+            int out_hm = -goe, out_f = -gep;
+            int2 sp_cur = make_int2(-goe, -gep), sp_next = make_int2(-goe, -gep);
+            if (!first) {
+                if (lane < n) sp_cur = spill[lane];
+                if (32 + lane < n) sp_next = spill[32 + lane];
+            }
+            const int steps = n + kWarp - 1;
+            for (int t = 0; t < steps; ++t) {
+                if ((t & 31) == 0 && t > 0) {
+                    sp_cur = sp_next;
+                    if (!first && t + 32 + lane < n) sp_next = spill[t + 32 + lane];
+                }
+                const int up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
+                const int up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
+                const int src = t & 31;
+                const int l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
+                const int l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                const int j = t - lane;
+                if (j >= 0 && j < n) {
+                    int F = lane == 0 ? l0_f : up_f;                 // F(r0, j)
+                    int d = hm_prev;                                 // (H - Goe)(r0 - 1, j - 1)
+                    hm_prev = lane == 0 ? l0_hm : up_hm;             // (H - Goe)(r0 - 1, j)
+                    const int4* prow =
+                        reinterpret_cast<const int4*>(s_prof + subj[j] * kPStride + lane * kTB);
+#pragma unroll
+                    for (int r4 = 0; r4 < kTB; r4 += 4) {
+                        const int4 sv = prow[r4 >> 2];
+                        const int sc[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                        for (int h = 0; h < 4; h += 2) {
+                            const int r = r4 + h;
+                            const int x0 = __viaddmax_s32_relu(d, sc[h], E[r]);
+                            const int xm0 = x0 - goe;
+                            d = Hm[r];
+                            Hm[r] = __viaddmax_s32(F, -goe, xm0);
+                            E[r] = __viaddmax_s32(E[r], -ge, Hm[r]);
+                            F = __viaddmax_s32(F, -gep, xm0);
+                            const int x1 = __viaddmax_s32_relu(d, sc[h + 1], E[r + 1]);
+                            const int xm1 = x1 - goe;
+                            d = Hm[r + 1];
+                            Hm[r + 1] = __viaddmax_s32(F, -goe, xm1);
+                            E[r + 1] = __viaddmax_s32(E[r + 1], -ge, Hm[r + 1]);
+                            F = __viaddmax_s32(F, -gep, xm1);
+                            best = __vimax3_s32(best, x0, x1);
+                        }
+                    }
+                    out_hm = Hm[kTB - 1];
+                    out_f = F;
+                    if (lane == kWarp - 1 && !last) spill[j] = make_int2(out_hm, out_f);
+                }
+            }
+            __syncwarp();   // lane 31's spill writes are visible to the warp's next pass
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (seq >= 0 && lane == 0) qd.scores[seq] = best;
+    }
+}
+
+}  // namespace
+
+size_t intra_block_smem_bytes(int alphabet1) {
+    return static_cast<size_t>(alphabet1) * kPStride * sizeof(int32_t);
+}
+
+int intra_block_occupancy(int alphabet1) {
+    int n = 0;
+    const size_t smem = intra_block_smem_bytes(alphabet1);
+    cudaFuncSetAttribute(k_intra_block_i32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intra_block_i32, kBBlock, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int intra_block_threads_b() { return kBBlock; }
+
+// Runs the long-subject (kIntraLong) and routed-group (kIntraGroups) work sources.
+cudaError_t launch_intra_block(const IntraParams& p, int grid, cudaStream_t st) {
+    const size_t smem = intra_block_smem_bytes(p.alphabet1);
+    cudaError_t e = cudaFuncSetAttribute(k_intra_block_i32,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_intra_block_i32<<<grid, kBBlock, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace swgb

@@ -266,6 +266,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // Scratch shared by all plans of this database.
     P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]);
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
+    // the block variant shares the per-warp pass buffers: never more blocks than the generic grid
+    P.intra_block_grid = std::min(P.intra_grid, db->sms * db->intra_block_occ);
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
     const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
@@ -430,12 +432,14 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     } else {
         if (jp.num_long > 0) {
             jp.mode = kIntraLong;
-            CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_block_grid, st)
+                                      : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
         if (P.g_split < db->layout.num_groups) {
             jp.mode = kIntraGroups;
-            CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_block_grid, st)
+                                      : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
     }
@@ -667,6 +671,8 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     for (int v = 0; v < inter_mq_num_variants() && v < kMaxVariants; ++v)
         db->inter_mq_occ[v] = inter_mq_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
+    db->intra_block_occ = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0'
+                              ? 0 : intra_block_occupancy(alphabet_size + 1);
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
     const char* forced = std::getenv("SWGB_VARIANT");

@@ -61,7 +61,7 @@ struct Plan {
     int variant = 0;
     int64_t max_mpad = 0;
     int64_t num_items = 0;
-    int inter_grid = 0, intra_grid = 0;
+    int inter_grid = 0, intra_grid = 0, intra_block_grid = 0;
     uint32_t flag_cap = 0;
     int64_t cells = 0, inter_cells = 0, launches = 0;
     DevBuf<int16_t> qp;
@@ -122,6 +122,7 @@ struct sw_db {
     int inter_occ[swgb::kMaxVariants] = {};
     int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;
+    int intra_block_occ = 0;
     // last search
     sw_stats stats{};
     bool stats_pending = false;

@@ -276,38 +276,60 @@ bool build_tick(sw_server* s, int32_t c, const std::vector<Request*>& act) {
         t.mq_steps = 0;
         return false;
     }
-    // Two streams of T-row strips, balanced by strip count, longest query first.
+    // Independent batches, each with two streams of T-row strips balanced by strip count,
+    // longest query first.  As few batches as give ~12 waves of work items (larger batches
+    // balance their two streams better), and at least four requests per batch.
     std::vector<Request*> order(act.begin(), act.end());
     std::stable_sort(order.begin(), order.end(), [](Request* a, Request* b) { return a->m > b->m; });
-    std::vector<Request*> stream[2];
-    int64_t len[2] = {0, 0};
+    const int64_t g0s = c0 * s->W, g1s = std::min<int64_t>(c1 * s->W, s->db->layout.num_groups);
+    const int64_t n_hb = std::max<int64_t>(1, (2 * (g1s - g0s) + s->W - 1) / s->W);
+    const int64_t want = (12 * static_cast<int64_t>(s->mq_grid) + n_hb - 1) / n_hb;
+    const int nb = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>(want, static_cast<int64_t>(order.size()) / 4)));
+    std::vector<std::vector<Request*>> batch(static_cast<size_t>(nb));
+    std::vector<int64_t> bload(static_cast<size_t>(nb), 0);
     for (Request* r : order) {
-        const int x = len[0] <= len[1] ? 0 : 1;
-        stream[x].push_back(r);
-        len[x] += (r->m + s->T - 1) / s->T;
+        const size_t b = static_cast<size_t>(std::min_element(bload.begin(), bload.end()) - bload.begin());
+        batch[b].push_back(r);
+        bload[b] += (r->m + s->T - 1) / s->T;
     }
-    const int64_t n = std::max(len[0], len[1]);
-    for (int64_t k = 0; k < n; ++k) s->steps_h[k] = MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0};
-    for (int x = 0; x < 2; ++x) {
-        int64_t k = 0;
-        for (Request* r : stream[x]) {
-            const int32_t S = (r->m + s->T - 1) / s->T;
-            for (int32_t si = 0; si < S; ++si, ++k) {
-                MqStep& st = s->steps_h[k];
-                uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
-                if (si == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
-                if (si == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
-                st.flags = fl;
-                if (x == 0) {
-                    st.qa = r->slot;
-                    st.sa = si;
-                } else {
-                    st.qb = r->slot;
-                    st.sb = si;
+    int64_t off = 0;
+    t.n_batches = nb;
+    for (int b = 0; b < nb; ++b) {
+        t.batch_step_off[b] = static_cast<int32_t>(off);
+        std::vector<Request*> stream[2];
+        int64_t len[2] = {0, 0};
+        for (Request* r : batch[static_cast<size_t>(b)]) {
+            const int x = len[0] <= len[1] ? 0 : 1;
+            stream[x].push_back(r);
+            len[x] += (r->m + s->T - 1) / s->T;
+        }
+        const int64_t n = std::max(len[0], len[1]);
+        for (int64_t k = 0; k < n; ++k) s->steps_h[off + k] = MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0};
+        for (int x = 0; x < 2; ++x) {
+            int64_t k = off;
+            for (Request* r : stream[x]) {
+                const int32_t S = (r->m + s->T - 1) / s->T;
+                for (int32_t si = 0; si < S; ++si, ++k) {
+                    MqStep& st = s->steps_h[k];
+                    uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
+                    if (si == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
+                    if (si == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
+                    st.flags = fl;
+                    if (x == 0) {
+                        st.qa = r->slot;
+                        st.sa = si;
+                    } else {
+                        st.qb = r->slot;
+                        st.sb = si;
+                    }
                 }
             }
         }
+        off += n;
     }
+    t.batch_step_off[nb] = static_cast<int32_t>(off);
+    const int64_t n = off;
     const int64_t g0 = c0 * s->W, g1 = std::min<int64_t>(c1 * s->W, s->db->layout.num_groups);
     t.mq_steps = static_cast<int32_t>(n);
     t.hg_begin = static_cast<int32_t>(2 * g0);
@@ -444,7 +466,7 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     s->opt.max_inflight = 32;
     s->opt.max_query_len = 8192;
     s->opt.state_budget_bytes = int64_t{1} << 30;
-    s->opt.slices = 8;
+    s->opt.slices = 0;
     s->opt.max_pending = 4096;
     if (opts) {
         if (opts->max_inflight > 0) s->opt.max_inflight = opts->max_inflight;
@@ -462,9 +484,14 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     s->W = inter_variant_warps(s->variant);
     s->T = inter_mq_variant_rows(s->variant);
     s->nchunks = (v.num_groups + s->W - 1) / s->W;
-    // Slices of about equal residue work, whole chunks of W groups each.
+    // Slices of about equal residue work, whole chunks of W groups each.  Default: as many as
+    // keep eight waves of multi-query work items per tick.
     {
-        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(s->opt.slices, s->nchunks));
+        const int64_t warps = static_cast<int64_t>(v.sms) * std::max(1, db->inter_mq_occ[s->variant]) * s->W;
+        const int64_t auto_k = std::max<int64_t>(1, std::min<int64_t>(16, 2 * v.num_groups / std::max<int64_t>(1, 8 * warps)));
+        const int64_t want = s->opt.slices > 0 ? s->opt.slices : auto_k;
+        s->opt.slices = static_cast<int32_t>(want);
+        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(want, s->nchunks));
         std::vector<int64_t> cres(static_cast<size_t>(s->nchunks) + 1, 0);
         for (int64_t c = 0; c < s->nchunks; ++c) {
             int64_t r = 0;
@@ -488,7 +515,8 @@ sw_status sw_server_create(sw_db* db, const int8_t* matrix, int32_t gap_open, in
     s->mpad_max = (s->opt.max_query_len + kQpRows - 1) / kQpRows * kQpRows;
     s->max_steps = std::max<int64_t>(1, static_cast<int64_t>(s->opt.max_inflight) *
                                             ((s->opt.max_query_len + s->T - 1) / s->T));
-    s->rows_pad = (s->max_steps * s->T + kQpRows - 1) / kQpRows * kQpRows;
+    // a batch may start at any step and its staging window reads kQpRows rows from there
+    s->rows_pad = (s->max_steps * s->T + 2 * kQpRows - 1) / kQpRows * kQpRows;
     const int S = s->opt.max_inflight;
     SCU(s->q_buf.ensure(static_cast<size_t>(S) * s->opt.max_query_len));
     SCU(s->qp_buf.ensure(static_cast<size_t>(S) * (s->A + 1) * s->mpad_max));

@@ -46,8 +46,10 @@ constexpr int kTickMax = 128;
 struct TickDesc {
     int32_t n;                        // requests in this tick
     int32_t n_long;                   // requests whose long subjects run in this tick
-    int32_t mq_steps;                 // multi-query ticks: strip pairs of the two streams
+    int32_t mq_steps;                 // multi-query ticks: strip pairs of all batches
     int32_t hg_begin, hg_end;         // multi-query ticks: half-groups of the database slice
+    int32_t n_batches;                // multi-query ticks: independent two-stream batches
+    int32_t batch_step_off[kTickMax + 1];   // batch b owns steps [off[b], off[b+1])
     int32_t slot[kTickMax];           // query slot of request s
     int32_t chunk_end[kTickMax];      // its chunks [chunk_end - count, chunk_end), longest first
     int32_t prefix[kTickMax + 1];     // item offsets: request s owns items [prefix[s], prefix[s+1])
@@ -187,6 +189,10 @@ cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, con
                             int32_t bias, uint32_t* d_pp, int64_t rows_pad, Control* ctrl,
                             cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
+// Block-shared-profile variant for the kIntraLong and kIntraGroups work sources (4 warps).
+size_t intra_block_smem_bytes(int alphabet1);
+int intra_block_occupancy(int alphabet1);
+cudaError_t launch_intra_block(const IntraParams& p, int grid, cudaStream_t st);
 int intra_block_threads();
 int intra_rows_per_pass();
 size_t intra_smem_bytes(int alphabet1);

@@ -133,7 +133,11 @@ def test_saturating_hits_rescored_exactly(sw, flag_cap, monkeypatch):
     assert exp[0][idx].max() > 32767 and st["flagged"] >= 6
 
 
-def test_long_subjects_intra_kernel(sw):
+@pytest.mark.parametrize("block", ["1", "0"])
+def test_long_subjects_intra_kernel(sw, block, monkeypatch):
+    """Subjects above the cutoff on the int32 intra-task kernel: the block-shared-profile
+    variant (default) and the per-warp variant (SWGB_INTRA_BLOCK=0)."""
+    monkeypatch.setenv("SWGB_INTRA_BLOCK", block)
     rng = np.random.default_rng(9)
     lens = np.concatenate([rng.integers(1, 300, size=120), rng.integers(1000, 2600, size=9), [4097]])
     db = w.database_from_lengths(rng, lens)
