@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as w  # noqa: E402
 
-# ALU-pipe roofline of the inter-task kernel (derivation in the design doc): the DPX max-plus
+# ALU-pipe roofline of the inter-task kernel: the DPX max-plus
 # operations issue on the ALU pipe at 64 lane-operations per clock per SM (ncu: the pipe is
 # 92% busy at 0.52 IPC per sub-partition; wall-clock probe: 18.9e12 lane-ops/s at 2,070 MHz
 # on 152 SMs), two cells per int16x2 lane-operation, and at least 5.5 ALU operations per cell

@@ -198,7 +198,7 @@ struct MqVariant {
 };
 
 const MqVariant kMqVariants[] = {
-    {32, 4, reinterpret_cast<const void*>(&k_inter_mq_i16x2<32, 4, 4>)},
+    {32, 4, reinterpret_cast<const void*>(&k_inter_mq_i16x2<32, 4, 3>)},
     {64, 4, reinterpret_cast<const void*>(&k_inter_mq_i16x2<64, 4, 2>)},
     {32, 8, reinterpret_cast<const void*>(&k_inter_mq_i16x2<32, 8, 2>)},
     {64, 8, reinterpret_cast<const void*>(&k_inter_mq_i16x2<64, 8, 1>)},
@@ -279,7 +279,7 @@ cudaError_t launch_inter_mq(const InterMqParams& p, int variant, int grid, cudaS
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     switch (variant) {
-        case 0: launch_mq_variant<32, 4, 4>(p, grid, smem, st); break;
+        case 0: launch_mq_variant<32, 4, 3>(p, grid, smem, st); break;
         case 1: launch_mq_variant<64, 4, 2>(p, grid, smem, st); break;
         case 2: launch_mq_variant<32, 8, 2>(p, grid, smem, st); break;
         default: launch_mq_variant<64, 8, 1>(p, grid, smem, st); break;
