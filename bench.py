@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner")
     ap.add_argument("--variant", type=int, default=-1,
                     help="force an inter-task kernel variant instead of autotuning (profiling)")
+    ap.add_argument("--placement", default="device", choices=["device", "host"],
+                    help="database in HBM (default) or streamed from pinned host memory")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-query-per-launch comparison")
     return ap.parse_args()
@@ -260,7 +262,8 @@ def run_ours(args, world, rank, local):
     cat = np.concatenate(wl.queries)
     qoff = np.zeros(nq + 1, np.int64)
     np.cumsum([len(q) for q in wl.queries], out=qoff[1:])
-    db = sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE)
+    db = sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE,
+                       placement=sw.PLACE_HOST if args.placement == "host" else sw.PLACE_DEVICE)
     N = db.num_seqs
     d_q = torch.from_numpy(cat).cuda()
     d_s = torch.empty(nq * N, dtype=torch.int32, device="cuda")
@@ -406,6 +409,7 @@ def run_ours(args, world, rank, local):
                        "db_residues": wl.db.num_residues, "cells_per_step": cells,
                        "kernel_variant": tune,
                        "per_gpu": "each rank searches its own database of this size",
+                       "placement": args.placement,
                        "l2": f"inputs larger than L2 (database {wl.db.num_residues / 1e6:.0f} MB "
                              "resident in HBM, read once per query per step)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),

@@ -59,8 +59,16 @@ typedef struct {
                               (default 3072; must be a multiple of 8) */
     int32_t flag_cap;      /* capacity of the list of saturated int16 lanes (default 2^20);
                               when more lanes saturate, the rescore sweeps every score */
-    int32_t reserved[5];
+    int32_t placement;     /* SW_PLACE_DEVICE (default): the database is copied to HBM.
+                              SW_PLACE_HOST: the database stays in pinned host memory mapped
+                              into the device address space, and the kernels stream it over
+                              the CPU-GPU link while they compute -- for databases larger than
+                              HBM (the paper's future work, Section 6). */
+    int32_t reserved[4];
 } sw_db_options;
+
+#define SW_PLACE_DEVICE 0
+#define SW_PLACE_HOST 1
 
 /* Per-call measurements of the last search on a handle (CUDA events on the launch stream). */
 typedef struct {

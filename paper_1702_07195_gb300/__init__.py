@@ -33,7 +33,11 @@ STATUS = {0: "SW_OK", -1: "SW_ERR_ARG", -2: "SW_ERR_CODE", -3: "SW_ERR_OOM", -4:
 
 class DbOptions(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("long_cutoff", ctypes.c_int32),
-                ("flag_cap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("flag_cap", ctypes.c_int32), ("placement", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+PLACE_DEVICE, PLACE_HOST = 0, 1
 
 
 class Stats(ctypes.Structure):
@@ -204,8 +208,11 @@ class Database:
 
 
 def sw_db_load(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 0,
-               device: int = 0, flag_cap: int = 0) -> Database:
-    """Preprocess and upload a database (residues uint8 codes, offsets int64[N+1])."""
+               device: int = 0, flag_cap: int = 0, placement: int = PLACE_DEVICE) -> Database:
+    """Preprocess and upload a database (residues uint8 codes, offsets int64[N+1]).
+
+    placement=PLACE_HOST keeps it in pinned host memory that the kernels stream over the
+    CPU-GPU link (databases larger than device memory)."""
     r = _u8(residues)
     o = np.ascontiguousarray(offsets, dtype=np.int64)
     n = int(o.shape[0] - 1)
@@ -213,6 +220,7 @@ def sw_db_load(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 0,
     opts.device = int(device)
     opts.long_cutoff = int(long_cutoff)
     opts.flag_cap = int(flag_cap)
+    opts.placement = int(placement)
     h = _vp()
     _check(lib.sw_db_load_ex(_ptr(r, _u8p), _ptr(o, _i64p), n, int(alphabet_size),
                              ctypes.byref(opts), ctypes.byref(h)))

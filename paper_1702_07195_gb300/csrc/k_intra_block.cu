@@ -15,13 +15,8 @@ namespace swgb {
 
 namespace {
 
-constexpr int kTB = 16;                      // query rows per lane
-constexpr int kRowsB = kTB * kWarp;          // 512 rows per pass
 constexpr int kBW = 4;                       // warps per block = subjects per block item
 constexpr int kBBlock = kBW * kWarp;
-constexpr int kPStride = kRowsB + 4;         // int32 per shared-memory profile row
-
-static_assert(kRowsB % kQpRows == 0, "profiles are padded to multiples of kQpRows");
 
 struct BlockItem {
     int q;
@@ -60,7 +55,12 @@ __device__ bool decode_item(const IntraParams& p, unsigned long long it, BlockIt
     return true;
 }
 
+// kTB query rows per lane: passes of 32 * kTB rows (256 or 512).
+template <int kTB>
 __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p) {
+    constexpr int kRowsB = kTB * kWarp;
+    constexpr int kPStride = kRowsB + 4;     // int32 per shared-memory profile row
+    static_assert(kRowsB % kQpRows == 0, "profiles are padded to multiples of kQpRows");
     extern __shared__ __align__(16) int32_t s_prof[];     // (A+1) x kPStride
     __shared__ BlockItem s_item;
     __shared__ int s_done;
@@ -173,31 +173,33 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
 
 }  // namespace
 
-size_t intra_block_smem_bytes(int alphabet1) {
-    return static_cast<size_t>(alphabet1) * kPStride * sizeof(int32_t);
+size_t intra_block_smem_bytes(int rows_per_lane, int alphabet1) {
+    return static_cast<size_t>(alphabet1) * (rows_per_lane * kWarp + 4) * sizeof(int32_t);
 }
 
-int intra_block_occupancy(int alphabet1) {
+int intra_block_occupancy(int rows_per_lane, int alphabet1) {
     int n = 0;
-    const size_t smem = intra_block_smem_bytes(alphabet1);
-    cudaFuncSetAttribute(k_intra_block_i32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intra_block_i32, kBBlock, smem) !=
-        cudaSuccess)
-        return 0;
+    const size_t smem = intra_block_smem_bytes(rows_per_lane, alphabet1);
+    const void* fn = rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_intra_block_i32<8>)
+                                        : reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBBlock, smem) != cudaSuccess) return 0;
     return n;
 }
 
-int intra_block_threads_b() { return kBBlock; }
-
-// Runs the long-subject (kIntraLong) and routed-group (kIntraGroups) work sources.
-cudaError_t launch_intra_block(const IntraParams& p, int grid, cudaStream_t st) {
-    const size_t smem = intra_block_smem_bytes(p.alphabet1);
-    cudaError_t e = cudaFuncSetAttribute(k_intra_block_i32,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Runs the long-subject (kIntraLong) and routed-group (kIntraGroups) work sources with 8 or 16
+// query rows per lane.
+cudaError_t launch_intra_block(const IntraParams& p, int rows_per_lane, int grid, cudaStream_t st) {
+    const size_t smem = intra_block_smem_bytes(rows_per_lane, p.alphabet1);
+    const void* fn = rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_intra_block_i32<8>)
+                                        : reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    k_intra_block_i32<<<grid, kBBlock, smem, st>>>(p);
+    if (rows_per_lane == 8)
+        k_intra_block_i32<8><<<grid, kBBlock, smem, st>>>(p);
+    else
+        k_intra_block_i32<16><<<grid, kBBlock, smem, st>>>(p);
     return cudaGetLastError();
 }
 

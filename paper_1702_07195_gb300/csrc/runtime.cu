@@ -3,6 +3,7 @@
 // of saturated lanes), cached launch plans replayed as CUDA graphs, and the C ABI declared in
 // include/swgb.h.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -218,7 +219,16 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // max(inter work / rate, longest inter item) + routed work / intra rate.
     {
         const double scale = db->sms / 152.0;
-        const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale, r_intra = 2.4e12 * scale;
+        // the int32 kernel computes whole 512-row passes: charge it for the padded rows
+        double padded = 0.0, real = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double mq = P.m[static_cast<size_t>(q)];
+            real += mq;
+            padded += std::min(std::ceil(mq / 256.0) * 256.0 * (5.5 + 10.0 / 8) / (5.5 + 10.0 / 16),
+                               std::ceil(mq / 512.0) * 512.0);
+        }
+        const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale;
+        const double r_intra = 3.0e12 * scale * (padded > 0 ? real / padded : 1.0);
         const int64_t warps = static_cast<int64_t>(db->sms) *
                               std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]) * W;
         double sum_m = 0, max_m = 0;
@@ -266,8 +276,20 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // Scratch shared by all plans of this database.
     P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]);
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
+    // Rows per lane of the block int32 kernel: the fewer padded rows (with a per-step overhead
+    // of about 10 operations per lane against 5.5 per cell) the better.
+    {
+        double cost[2] = {0.0, 0.0};
+        const int tis[2] = {8, 16};
+        for (int v = 0; v < 2; ++v)
+            for (int q = 0; q < nq; ++q) {
+                const double rows = 32.0 * tis[v];
+                cost[v] += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (5.5 + 10.0 / tis[v]);
+            }
+        P.intra_rows_per_lane = cost[0] < cost[1] ? 8 : 16;
+    }
     // the block variant shares the per-warp pass buffers: never more blocks than the generic grid
-    P.intra_block_grid = std::min(P.intra_grid, db->sms * db->intra_block_occ);
+    P.intra_block_grid = std::min(P.intra_grid, db->sms * db->intra_block_occ[P.intra_rows_per_lane == 8 ? 0 : 1]);
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
     const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
@@ -312,7 +334,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
 
     const Gaps gaps{goe, ge, std::min(goe, ge)};
     InterParams& ip = P.inter;
-    ip.inter = db->inter.ptr;
+    ip.inter = db->inter_ptr;
     ip.group_off = db->group_off.ptr;
     ip.group_len = db->group_len.ptr;
     ip.perm = db->perm.ptr;
@@ -329,7 +351,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     ip.gaps = gaps;
     if (P.mq) {
         InterMqParams& mp = P.inter_mq;
-        mp.inter = db->inter.ptr;
+        mp.inter = db->inter_ptr;
         mp.group_off = db->group_off.ptr;
         mp.group_len = db->group_len.ptr;
         mp.perm = db->perm.ptr;
@@ -350,7 +372,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         mp.tick = nullptr;
     }
     IntraParams& jp = P.intra;
-    jp.plain = db->plain.ptr;
+    jp.plain = db->plain_ptr;
     jp.plain_off = db->plain_off.ptr;
     jp.queries = P.descs.ptr;
     jp.num_queries = nq;
@@ -432,13 +454,13 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     } else {
         if (jp.num_long > 0) {
             jp.mode = kIntraLong;
-            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_block_grid, st)
+            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_rows_per_lane, P.intra_block_grid, st)
                                       : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
         if (P.g_split < db->layout.num_groups) {
             jp.mode = kIntraGroups;
-            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_block_grid, st)
+            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_rows_per_lane, P.intra_block_grid, st)
                                       : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
@@ -581,11 +603,11 @@ bool db_view(const sw_db* db, DbView* v) {
     v->flag_cap = db->flag_cap;
     v->inter_occ = db->inter_occ[0];
     v->intra_occ = db->intra_occ;
-    v->inter = db->inter.ptr;
+    v->inter = db->inter_ptr;
     v->group_off = db->group_off.ptr;
     v->group_len = db->group_len.ptr;
     v->perm = db->perm.ptr;
-    v->plain = db->plain.ptr;
+    v->plain = db->plain_ptr;
     v->plain_off = db->plain_off.ptr;
     v->long_ids = db->long_ids.ptr;
     return true;
@@ -650,12 +672,15 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
         if (opts->device > 0) dev = opts->device;
         if (opts->long_cutoff > 0) cutoff = opts->long_cutoff;
         if (opts->flag_cap < 0) return fail(SW_ERR_ARG, "flag_cap < 0");
+        if (opts->placement != SW_PLACE_DEVICE && opts->placement != SW_PLACE_HOST)
+            return fail(SW_ERR_ARG, "placement must be SW_PLACE_DEVICE or SW_PLACE_HOST");
     }
     std::unique_ptr<sw_db> db(new sw_db());
     db->device = dev;
     db->A = alphabet_size;
     db->long_cutoff = cutoff;
     if (opts && opts->flag_cap > 0) db->flag_cap = opts->flag_cap;
+    if (opts) db->placement = opts->placement;
     const std::string err = plan_layout(offsets, num_seqs, cutoff, db->layout);
     if (!err.empty()) return fail(SW_ERR_ARG, "%s", err.c_str());
     const int64_t R = num_seqs > 0 ? offsets[num_seqs] : 0;
@@ -671,8 +696,9 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     for (int v = 0; v < inter_mq_num_variants() && v < kMaxVariants; ++v)
         db->inter_mq_occ[v] = inter_mq_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
-    db->intra_block_occ = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0'
-                              ? 0 : intra_block_occupancy(alphabet_size + 1);
+    const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
+    db->intra_block_occ[0] = block_off ? 0 : intra_block_occupancy(8, alphabet_size + 1);
+    db->intra_block_occ[1] = block_off ? 0 : intra_block_occupancy(16, alphabet_size + 1);
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
     const char* forced = std::getenv("SWGB_VARIANT");
@@ -684,10 +710,21 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     CU(cudaStreamCreateWithFlags(&db->capture_stream, cudaStreamNonBlocking));
     for (auto& e : db->ev) CU(cudaEventCreate(&e));
     const Layout& L = db->layout;
-    std::vector<uint8_t> inter(static_cast<size_t>(std::max<int64_t>(L.inter_bytes, 1)));
-    if (L.num_groups > 0) fill_inter(residues, offsets, alphabet_size, L, inter.data());
-    CU(db->inter.ensure(inter.size()));
-    CU(cudaMemcpy(db->inter.ptr, inter.data(), inter.size(), cudaMemcpyHostToDevice));
+    const size_t inter_bytes = static_cast<size_t>(std::max<int64_t>(L.inter_bytes, 16));
+    if (db->placement == SW_PLACE_HOST) {
+        // pinned host memory mapped into the device address space: kernels read it over the link
+        CU(cudaHostAlloc(reinterpret_cast<void**>(&db->host_inter), inter_bytes, cudaHostAllocMapped));
+        if (L.num_groups > 0) fill_inter(residues, offsets, alphabet_size, L, db->host_inter);
+        void* dp = nullptr;
+        CU(cudaHostGetDevicePointer(&dp, db->host_inter, 0));
+        db->inter_ptr = static_cast<const uint8_t*>(dp);
+    } else {
+        std::vector<uint8_t> inter(inter_bytes);
+        if (L.num_groups > 0) fill_inter(residues, offsets, alphabet_size, L, inter.data());
+        CU(db->inter.ensure(inter.size()));
+        CU(cudaMemcpy(db->inter.ptr, inter.data(), inter.size(), cudaMemcpyHostToDevice));
+        db->inter_ptr = db->inter.ptr;
+    }
     CU(db->group_off.ensure(L.group_off.size()));
     CU(db->group_len.ensure(L.group_len.size()));
     CU(db->perm.ensure(L.perm.size()));
@@ -699,8 +736,18 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
         CU(cudaMemcpy(db->perm.ptr, L.perm.data(), sizeof(int32_t) * L.perm.size(),
                       cudaMemcpyHostToDevice));
     }
-    CU(db->plain.ensure(static_cast<size_t>(std::max<int64_t>(R, 16))));
-    if (R > 0) CU(cudaMemcpy(db->plain.ptr, residues, static_cast<size_t>(R), cudaMemcpyHostToDevice));
+    if (db->placement == SW_PLACE_HOST) {
+        CU(cudaHostAlloc(reinterpret_cast<void**>(&db->host_plain),
+                         static_cast<size_t>(std::max<int64_t>(R, 16)), cudaHostAllocMapped));
+        if (R > 0) std::memcpy(db->host_plain, residues, static_cast<size_t>(R));
+        void* dp = nullptr;
+        CU(cudaHostGetDevicePointer(&dp, db->host_plain, 0));
+        db->plain_ptr = static_cast<const uint8_t*>(dp);
+    } else {
+        CU(db->plain.ensure(static_cast<size_t>(std::max<int64_t>(R, 16))));
+        if (R > 0) CU(cudaMemcpy(db->plain.ptr, residues, static_cast<size_t>(R), cudaMemcpyHostToDevice));
+        db->plain_ptr = db->plain.ptr;
+    }
     CU(db->plain_off.ensure(static_cast<size_t>(num_seqs) + 1));
     CU(cudaMemcpy(db->plain_off.ptr, offsets, sizeof(int64_t) * (num_seqs + 1), cudaMemcpyHostToDevice));
     CU(db->long_ids.ensure(std::max<size_t>(L.long_ids.size(), 1)));

@@ -62,6 +62,7 @@ struct Plan {
     int64_t max_mpad = 0;
     int64_t num_items = 0;
     int inter_grid = 0, intra_grid = 0, intra_block_grid = 0;
+    int intra_rows_per_lane = 16;
     uint32_t flag_cap = 0;
     int64_t cells = 0, inter_cells = 0, launches = 0;
     DevBuf<int16_t> qp;
@@ -103,6 +104,11 @@ struct sw_db {
     swgb::DevBuf<uint8_t> plain;
     swgb::DevBuf<int64_t> plain_off;
     swgb::DevBuf<int32_t> long_ids;
+    int32_t placement = 0;
+    uint8_t* host_inter = nullptr;   // SW_PLACE_HOST: pinned, mapped database copies
+    uint8_t* host_plain = nullptr;
+    const uint8_t* inter_ptr = nullptr;   // device view of the interleaved groups
+    const uint8_t* plain_ptr = nullptr;   // device view of the plain copy
     // scratch shared by all searches on this database (ordered on the device by ev[4])
     swgb::DevBuf<swgb::Control> ctrl;
     swgb::DevBuf<swgb::FlagEntry> flags;
@@ -122,9 +128,13 @@ struct sw_db {
     int inter_occ[swgb::kMaxVariants] = {};
     int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;
-    int intra_block_occ = 0;
+    int intra_block_occ[2] = {0, 0};   // 8 and 16 query rows per lane
     // last search
     sw_stats stats{};
     bool stats_pending = false;
     std::mutex mu;
+    ~sw_db() {
+        if (host_inter) cudaFreeHost(host_inter);
+        if (host_plain) cudaFreeHost(host_plain);
+    }
 };

@@ -189,10 +189,11 @@ cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, con
                             int32_t bias, uint32_t* d_pp, int64_t rows_pad, Control* ctrl,
                             cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
-// Block-shared-profile variant for the kIntraLong and kIntraGroups work sources (4 warps).
-size_t intra_block_smem_bytes(int alphabet1);
-int intra_block_occupancy(int alphabet1);
-cudaError_t launch_intra_block(const IntraParams& p, int grid, cudaStream_t st);
+// Block-shared-profile variant for the kIntraLong and kIntraGroups work sources (4 warps,
+// 8 or 16 query rows per lane).
+size_t intra_block_smem_bytes(int rows_per_lane, int alphabet1);
+int intra_block_occupancy(int rows_per_lane, int alphabet1);
+cudaError_t launch_intra_block(const IntraParams& p, int rows_per_lane, int grid, cudaStream_t st);
 int intra_block_threads();
 int intra_rows_per_pass();
 size_t intra_smem_bytes(int alphabet1);

@@ -343,3 +343,19 @@ def test_sorting_stage_after_search(sw):
     order = np.lexsort((np.arange(len(exp)), -exp))[:10]
     assert np.array_equal(top_i[0].cpu().numpy(), order)
     assert set(planted) <= set(order.tolist())
+
+
+def test_host_placement_streams_the_database(sw):
+    """SW_PLACE_HOST: the database stays in pinned host memory and the kernels read it over
+    the CPU-GPU link; scores are identical (long subjects and routed groups included)."""
+    rng = np.random.default_rng(17)
+    lens = np.concatenate([rng.integers(0, 400, size=500), rng.integers(3000, 5000, size=4)])
+    db = w.database_from_lengths(rng, lens)
+    qs = [w.draw_residues(rng, n) for n in (150, 700)]
+    sm = w.blosum62()
+    exp = _oracle_all(qs, db, sm, 10, 2)
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE, placement=sw.PLACE_HOST) as h:
+        got = sw.sw_search_batch(h, qs, sm, 10, 2)
+        got1 = sw.sw_search(h, qs[0], sm, 10, 2)
+    _check(got, exp, "host placement")
+    _check(got1[None], exp[:1], "host placement, one query")
