@@ -142,7 +142,6 @@ template <int kT, int kW, int kMinBlocks>
 __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const InterParams p) {
     constexpr int kBlock = kW * kWarp;
     extern __shared__ __align__(16) int16_t s_qp[];
-    __shared__ int s_item;
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
     const int qstride = kQpRows + kQpPad;
@@ -154,33 +153,31 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const In
     k.e0 = pack2(-p.gaps.gep);
     k.floor = 0x80008000u;
 
-    __shared__ InterItem s_tick_item;
+    __shared__ InterItem s_it;
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = static_cast<int>(atomicAdd(&p.ctrl->next_inter, 1u));
-            s_item = it;
+            InterItem next{-1, 0, 0, 0};   // query -1: no work left
             if (p.tick) {   // serving tick: decode (request, chunk) from the descriptor
                 const TickDesc* t = p.tick;
                 if (it < t->prefix[t->n]) {
                     int s = 0;
                     while (t->prefix[s + 1] <= it) ++s;
-                    const int chunk = t->chunk_end[s] - 1 - (it - t->prefix[s]);
-                    const int g0 = chunk * kW;
-                    s_tick_item = InterItem{t->slot[s], g0, min(kW, p.num_groups - g0), 0};
-                } else {
-                    s_item = 0x7fffffff;
+                    const int g0 = (t->chunk_end[s] - 1 - (it - t->prefix[s])) * kW;
+                    next = InterItem{t->slot[s], g0, min(kW, p.num_groups - g0), 0};
                 }
+            } else if (it < p.num_items) {
+                next = p.items[it];
             }
+            s_it = next;
         }
         __syncthreads();
-        const int it = s_item;
-        const InterItem item = p.tick ? s_tick_item : InterItem{};
+        const InterItem item = s_it;
         __syncthreads();
-        if (it >= (p.tick ? 0x7fffffff : p.num_items)) break;
-        const InterItem item_l = p.tick ? item : p.items[it];
-        const QueryDesc qd = p.queries[item_l.query];
-        const bool active = warp < item_l.ngroups;
-        const int g = item_l.group + warp;
+        if (item.query < 0) break;
+        const QueryDesc qd = p.queries[item.query];
+        const bool active = warp < item.ngroups;
+        const int g = item.group + warp;
         const int L = active ? p.group_len[g] : 0;
         const uint4* res =
             active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
@@ -208,8 +205,8 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const In
             const int base = g * kGroupSeqs + 2 * lane;
             const int b0 = static_cast<int>(static_cast<short>(best & 0xFFFFu));
             const int b1 = static_cast<int>(static_cast<short>(best >> 16));
-            emit(p, item_l.query, qd.scores, p.perm[base], b0);
-            emit(p, item_l.query, qd.scores, p.perm[base + 1], b1);
+            emit(p, item.query, qd.scores, p.perm[base], b0);
+            emit(p, item.query, qd.scores, p.perm[base + 1], b1);
         }
     }
 }

@@ -9,6 +9,16 @@
 // the block.  The slice is stored as int32 (sign-extended and biased once per pass, not once
 // per cell) and each lane owns 16 rows, halving the per-step shuffles and loads per cell.
 // Eqs. sw2-sw4, Section 2; the intra-task scheme of Section 1.
+//
+// Shared-memory layout of the slice: the 32 lanes read the rows of 32 different residues in
+// the same step, so with a plain row-major slice the bank a lane hits depends on its residue
+// and the 16-byte loads of a quarter-warp collide at random.  Here the row stride of a residue
+// is a multiple of 32 words (the residue no longer moves the bank) and lane l's chunk of
+// kTB words sits at a lane-dependent offset chosen so that the 8 lanes of every quarter-warp
+// start in 8 different 16-byte bank groups: each 16-byte profile load is one wavefront per
+// quarter-warp whatever the residues are.  With an odd number of rows per lane the chunks are
+// packed (lane l at word 5 l for 5 rows) and read with 4-byte loads: 5 l mod 32 is a
+// permutation of the banks, so those loads are conflict-free as they are.
 #include "swgb_device.cuh"
 
 namespace swgb {
@@ -55,18 +65,81 @@ __device__ bool decode_item(const IntraParams& p, unsigned long long it, BlockIt
     return true;
 }
 
-// kTB query rows per lane: passes of 32 * kTB rows (256 or 512).
+// Word offset of lane `lane`'s chunk of kTB rows inside one residue's slice row.  Chunks are
+// w = kTB / 4 bank groups (16 bytes each) wide and packed in w segments of 32 / w chunks, each
+// segment one group further along than a packed layout would put it; the lane -> (segment,
+// chunk) map gives the 8 lanes of a quarter-warp 8 distinct starting groups modulo 8.
+template <int kTB>
+__host__ __device__ constexpr int chunk_offset(int lane) {
+    if (kTB % 2 == 1) return kTB * lane;
+    constexpr int w = kTB / 4;
+    constexpr int per_q = 8 / w;                   // lanes of a quarter-warp per segment
+    const int q = lane >> 3, i = lane & 7;
+    const int seg = i / per_q, c = q * per_q + i % per_q;
+    return 4 * (33 * seg + w * c);
+}
+
+// Words per residue row of the slice: the span of the chunks rounded up to 32 words.
+template <int kTB>
+__host__ __device__ constexpr int slice_stride() {
+    return kTB % 2 == 1 ? (kTB * kWarp + 31) / 32 * 32 : (4 * (33 * (kTB / 4) - 1) + 31) / 32 * 32;
+}
+
+template <int kTB>
+constexpr bool chunks_conflict_free() {
+    if (kTB % 2 == 1) {
+        if (slice_stride<kTB>() % 32 != 0) return false;
+        for (int k = 0; k < kTB; ++k) {        // 4-byte loads: one bank per lane
+            unsigned long long seen = 0;
+            for (int l = 0; l < kWarp; ++l) seen |= 1ull << ((chunk_offset<kTB>(l) + k) % 32);
+            if (seen != 0xFFFFFFFFull) return false;
+        }
+        return true;
+    }
+    for (int q = 0; q < 4; ++q) {
+        unsigned seen = 0;
+        for (int i = 0; i < 8; ++i) {
+            const int off = chunk_offset<kTB>(8 * q + i);
+            if (off % 4 != 0) return false;
+            seen |= 1u << ((off / 4) % 8);
+        }
+        if (seen != 0xFFu) return false;
+    }
+    for (int l = 0; l < kWarp; ++l)                // chunks lie inside the row, disjoint
+        for (int m = 0; m < kWarp; ++m) {
+            const int a = chunk_offset<kTB>(l), b = chunk_offset<kTB>(m);
+            if (a + kTB > slice_stride<kTB>()) return false;
+            if (l != m && a < b + kTB && b < a + kTB) return false;
+        }
+    return true;
+}
+static_assert(chunks_conflict_free<5>() && chunks_conflict_free<8>() && chunks_conflict_free<16>(),
+              "profile slice layout");
+
+// One query row of the column step: the cell update of Eqs. sw2-sw4 on (H - Goe) state.
+__device__ __forceinline__ int cell_i32(int& d, int& hm, int& e, int& f, int sc, int goe, int ge,
+                                        int gep) {
+    const int x = __viaddmax_s32_relu(d, sc, e);
+    const int xm = x - goe;
+    d = hm;
+    hm = __viaddmax_s32(f, -goe, xm);
+    e = __viaddmax_s32(e, -ge, hm);
+    f = __viaddmax_s32(f, -gep, xm);
+    return x;
+}
+
+// kTB query rows per lane: passes of 32 * kTB rows (160, 256 or 512).
 template <int kTB>
 __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p) {
     constexpr int kRowsB = kTB * kWarp;
-    constexpr int kPStride = kRowsB + 4;     // int32 per shared-memory profile row
-    static_assert(kRowsB % kQpRows == 0, "profiles are padded to multiples of kQpRows");
+    constexpr int kPStride = slice_stride<kTB>();   // int32 per shared-memory profile row
     extern __shared__ __align__(16) int32_t s_prof[];     // (A+1) x kPStride
     __shared__ BlockItem s_item;
     __shared__ int s_done;
     __shared__ int s_passes;
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
+    const int my_chunk = chunk_offset<kTB>(lane);
     int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kBW + warp) * p.spill_stride;
     const int goe = p.gaps.goe, ge = p.gaps.ge, gep = p.gaps.gep;
     unsigned long long* counter =
@@ -100,7 +173,7 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
                 const int r = v - d * kRowsB;
                 const int64_t row = static_cast<int64_t>(pass) * kRowsB + r;
                 // rows past the profile score 0: S' = 0 + Goe, like the profile's own padding
-                s_prof[d * kPStride + r] =
+                s_prof[d * kPStride + chunk_offset<kTB>(r / kTB) + r % kTB] =
                     row < qd.m_pad ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + row] + p.qp_add : goe;
             }
             __syncthreads();
@@ -134,8 +207,17 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
                     int F = lane == 0 ? l0_f : up_f;                 // F(r0, j)
                     int d = hm_prev;                                 // (H - Goe)(r0 - 1, j - 1)
                     hm_prev = lane == 0 ? l0_hm : up_hm;             // (H - Goe)(r0 - 1, j)
-                    const int4* prow =
-                        reinterpret_cast<const int4*>(s_prof + subj[j] * kPStride + lane * kTB);
+                    const int32_t* prow1 = s_prof + subj[j] * kPStride + my_chunk;
+                    if constexpr (kTB % 2 == 1) {
+#pragma unroll
+                        for (int r = 0; r + 1 < kTB; r += 2) {
+                            const int x0 = cell_i32(d, Hm[r], E[r], F, prow1[r], goe, ge, gep);
+                            const int x1 = cell_i32(d, Hm[r + 1], E[r + 1], F, prow1[r + 1], goe, ge, gep);
+                            best = __vimax3_s32(best, x0, x1);
+                        }
+                        best = max(best, cell_i32(d, Hm[kTB - 1], E[kTB - 1], F, prow1[kTB - 1], goe, ge, gep));
+                    } else {
+                    const int4* prow = reinterpret_cast<const int4*>(prow1);
 #pragma unroll
                     for (int r4 = 0; r4 < kTB; r4 += 4) {
                         const int4 sv = prow[r4 >> 2];
@@ -158,6 +240,7 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
                             best = __vimax3_s32(best, x0, x1);
                         }
                     }
+                    }
                     out_hm = Hm[kTB - 1];
                     out_f = F;
                     if (lane == kWarp - 1 && !last) spill[j] = make_int2(out_hm, out_f);
@@ -173,30 +256,45 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
 
 }  // namespace
 
+namespace {
+
+const void* block_fn(int rows_per_lane) {
+    switch (rows_per_lane) {
+        case 5: return reinterpret_cast<const void*>(&k_intra_block_i32<5>);
+        case 8: return reinterpret_cast<const void*>(&k_intra_block_i32<8>);
+        default: return reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+    }
+}
+
+}  // namespace
+
 size_t intra_block_smem_bytes(int rows_per_lane, int alphabet1) {
-    return static_cast<size_t>(alphabet1) * (rows_per_lane * kWarp + 4) * sizeof(int32_t);
+    const int stride = rows_per_lane == 5   ? slice_stride<5>()
+                       : rows_per_lane == 8 ? slice_stride<8>()
+                                            : slice_stride<16>();
+    return static_cast<size_t>(alphabet1) * stride * sizeof(int32_t);
 }
 
 int intra_block_occupancy(int rows_per_lane, int alphabet1) {
     int n = 0;
     const size_t smem = intra_block_smem_bytes(rows_per_lane, alphabet1);
-    const void* fn = rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_intra_block_i32<8>)
-                                        : reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+    const void* fn = block_fn(rows_per_lane);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBBlock, smem) != cudaSuccess) return 0;
     return n;
 }
 
-// Runs the long-subject (kIntraLong) and routed-group (kIntraGroups) work sources with 8 or 16
-// query rows per lane.
+// Runs the long-subject (kIntraLong) and routed-group (kIntraGroups) work sources with 5, 8 or
+// 16 query rows per lane.
 cudaError_t launch_intra_block(const IntraParams& p, int rows_per_lane, int grid, cudaStream_t st) {
     const size_t smem = intra_block_smem_bytes(rows_per_lane, p.alphabet1);
-    const void* fn = rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_intra_block_i32<8>)
-                                        : reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+    const void* fn = block_fn(rows_per_lane);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    if (rows_per_lane == 8)
+    if (rows_per_lane == 5)
+        k_intra_block_i32<5><<<grid, kBBlock, smem, st>>>(p);
+    else if (rows_per_lane == 8)
         k_intra_block_i32<8><<<grid, kBBlock, smem, st>>>(p);
     else
         k_intra_block_i32<16><<<grid, kBBlock, smem, st>>>(p);

@@ -67,6 +67,12 @@ bool mq_enabled() {
     return !(v && v[0] == '0');
 }
 
+// Blocks per SM of the block int32 kernel (0: as many as fit).
+int forced_intra_blocks_per_sm() {
+    const char* v = std::getenv("SWGB_INTRA_BLOCKS_PER_SM");
+    return v ? std::max(0, std::atoi(v)) : 0;
+}
+
 }  // namespace
 
 namespace swgb {
@@ -219,13 +225,18 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // max(inter work / rate, longest inter item) + routed work / intra rate.
     {
         const double scale = db->sms / 152.0;
-        // the int32 kernel computes whole 512-row passes: charge it for the padded rows
+        // the int32 kernel computes whole passes of 32 x (5, 8 or 16) rows: charge it for the
+        // padded rows and the per-step overhead, relative to 16 rows per lane
         double padded = 0.0, real = 0.0;
         for (int q = 0; q < nq; ++q) {
             const double mq = P.m[static_cast<size_t>(q)];
             real += mq;
-            padded += std::min(std::ceil(mq / 256.0) * 256.0 * (5.5 + 10.0 / 8) / (5.5 + 10.0 / 16),
-                               std::ceil(mq / 512.0) * 512.0);
+            double c = 1e300;
+            for (int v = 0; v < 3; ++v) {
+                const double tb = kIntraBlockRows[v], rows = 32.0 * tb;
+                c = std::min(c, std::ceil(mq / rows) * rows * (5.5 + 10.0 / tb) / (5.5 + 10.0 / 16));
+            }
+            padded += c;
         }
         const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale;
         const double r_intra = 3.0e12 * scale * (padded > 0 ? real / padded : 1.0);
@@ -278,18 +289,38 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
     // Rows per lane of the block int32 kernel: the fewer padded rows (with a per-step overhead
     // of about 10 operations per lane against 5.5 per cell) the better.
+    int tb_index = 2;
     {
-        double cost[2] = {0.0, 0.0};
-        const int tis[2] = {8, 16};
-        for (int v = 0; v < 2; ++v)
+        double best_cost = 1e300;
+        for (int v = 0; v < 3; ++v) {
+            double cost = 0.0;
             for (int q = 0; q < nq; ++q) {
-                const double rows = 32.0 * tis[v];
-                cost[v] += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (5.5 + 10.0 / tis[v]);
+                const double rows = 32.0 * kIntraBlockRows[v];
+                cost += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (5.5 + 10.0 / kIntraBlockRows[v]);
             }
-        P.intra_rows_per_lane = cost[0] < cost[1] ? 8 : 16;
+            if (db->intra_block_occ[v] > 0 && cost < best_cost * 0.999) {
+                best_cost = cost;
+                tb_index = v;
+            }
+        }
+        P.intra_rows_per_lane = kIntraBlockRows[tb_index];
     }
     // the block variant shares the per-warp pass buffers: never more blocks than the generic grid
-    P.intra_block_grid = std::min(P.intra_grid, db->sms * db->intra_block_occ[P.intra_rows_per_lane == 8 ? 0 : 1]);
+    {
+        // With few block items (a small database), the search ends with the longest subjects'
+        // warps, each sharing its SM sub-partition with the other resident warps; at most three
+        // blocks per SM (three warps per sub-partition) shortens that tail more than it costs in
+        // latency hiding (measured: 10,000 sequences 0.38 -> 0.33 ms; a 50,000 x 20,000-residue
+        // database keeps four blocks per SM, which is 8 % faster there).
+        int per_sm = db->intra_block_occ[tb_index];
+        const int64_t n_subjects = static_cast<int64_t>(db->layout.long_ids.size()) +
+                                   static_cast<int64_t>(G - P.g_split) * kGroupSeqs;
+        const int64_t block_items = (n_subjects + 3) / 4 * nq;
+        if (block_items < 8LL * db->sms * per_sm) per_sm = std::min(per_sm, 3);
+        const int forced = forced_intra_blocks_per_sm();
+        if (forced > 0) per_sm = std::min(db->intra_block_occ[tb_index], forced);
+        P.intra_block_grid = std::min(P.intra_grid, db->sms * per_sm);
+    }
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
     const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
@@ -513,6 +544,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(mq_enabled() ? 1 : 0);
     key.push_back(forced_split());
     key.push_back(db->no_route ? 1 : 0);
+    key.push_back(forced_intra_blocks_per_sm());
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 
@@ -697,8 +729,8 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
         db->inter_mq_occ[v] = inter_mq_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
     const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
-    db->intra_block_occ[0] = block_off ? 0 : intra_block_occupancy(8, alphabet_size + 1);
-    db->intra_block_occ[1] = block_off ? 0 : intra_block_occupancy(16, alphabet_size + 1);
+    for (int v = 0; v < 3; ++v)
+        db->intra_block_occ[v] = block_off ? 0 : intra_block_occupancy(kIntraBlockRows[v], alphabet_size + 1);
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
     const char* forced = std::getenv("SWGB_VARIANT");

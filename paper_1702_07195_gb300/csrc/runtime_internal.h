@@ -128,7 +128,7 @@ struct sw_db {
     int inter_occ[swgb::kMaxVariants] = {};
     int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;
-    int intra_block_occ[2] = {0, 0};   // 8 and 16 query rows per lane
+    int intra_block_occ[3] = {0, 0, 0};   // 5, 8 and 16 query rows per lane
     // last search
     sw_stats stats{};
     bool stats_pending = false;

@@ -107,3 +107,34 @@ def test_server_rejects_and_times_out(sw):
             assert e.value.status == -5
             for t in tickets:
                 assert srv.wait(t).shape == (h.num_seqs,)
+
+
+def test_concurrent_clients(sw):
+    """Four client threads submit and wait at the same time; every result equals the
+    single-query search of the same query (the mix of one- and multi-request ticks)."""
+    wl = w.batched(seed=25, scale=0.008)
+    qs = w.serving_queries(20, seed=13)
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        ref = sw.sw_search_batch(h, qs, wl.matrix, 10, 2)
+        out = [None] * len(qs)
+        errors = []
+        with sw.Server(h, wl.matrix, 10, 2, max_inflight=6, slices=4) as srv:
+
+            def client(ids):
+                try:
+                    for i in ids:
+                        out[i] = srv.wait(srv.submit(qs[i]))
+                except Exception as exc:   # surfaced below
+                    errors.append(exc)
+
+            threads = [threading.Thread(target=client, args=(list(range(c, len(qs), 4)),))
+                       for c in range(4)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            st = srv.stats()
+    assert not errors, errors
+    for k in range(len(qs)):
+        assert np.array_equal(out[k], ref[k]), f"request {k}"
+    assert st["completed"] == len(qs)
