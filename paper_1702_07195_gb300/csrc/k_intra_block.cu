@@ -19,6 +19,8 @@
 // quarter-warp whatever the residues are.  With an odd number of rows per lane the chunks are
 // packed (lane l at word 5 l for 5 rows) and read with 4-byte loads: 5 l mod 32 is a
 // permutation of the banks, so those loads are conflict-free as they are.
+#include <type_traits>
+
 #include "swgb_device.cuh"
 
 namespace swgb {
@@ -87,31 +89,31 @@ __host__ __device__ constexpr int slice_stride() {
 
 template <int kTB>
 constexpr bool chunks_conflict_free() {
+    bool ok = slice_stride<kTB>() % 32 == 0;   // the residue does not move the bank
     if (kTB % 2 == 1) {
-        if (slice_stride<kTB>() % 32 != 0) return false;
         for (int k = 0; k < kTB; ++k) {        // 4-byte loads: one bank per lane
             unsigned long long seen = 0;
             for (int l = 0; l < kWarp; ++l) seen |= 1ull << ((chunk_offset<kTB>(l) + k) % 32);
-            if (seen != 0xFFFFFFFFull) return false;
+            ok = ok && seen == 0xFFFFFFFFull;
         }
-        return true;
-    }
-    for (int q = 0; q < 4; ++q) {
-        unsigned seen = 0;
-        for (int i = 0; i < 8; ++i) {
-            const int off = chunk_offset<kTB>(8 * q + i);
-            if (off % 4 != 0) return false;
-            seen |= 1u << ((off / 4) % 8);
+    } else {
+        for (int q = 0; q < 4; ++q) {          // 16-byte loads: 8 groups per quarter-warp
+            unsigned seen = 0;
+            for (int i = 0; i < 8; ++i) {
+                const int off = chunk_offset<kTB>(8 * q + i);
+                ok = ok && off % 4 == 0;
+                seen |= 1u << ((off / 4) % 8);
+            }
+            ok = ok && seen == 0xFFu;
         }
-        if (seen != 0xFFu) return false;
     }
-    for (int l = 0; l < kWarp; ++l)                // chunks lie inside the row, disjoint
+    for (int l = 0; l < kWarp; ++l)            // chunks lie inside the row, disjoint
         for (int m = 0; m < kWarp; ++m) {
             const int a = chunk_offset<kTB>(l), b = chunk_offset<kTB>(m);
-            if (a + kTB > slice_stride<kTB>()) return false;
-            if (l != m && a < b + kTB && b < a + kTB) return false;
+            ok = ok && a + kTB <= slice_stride<kTB>();
+            ok = ok && (l == m || a >= b + kTB || b >= a + kTB);
         }
-    return true;
+    return ok;
 }
 static_assert(chunks_conflict_free<5>() && chunks_conflict_free<8>() && chunks_conflict_free<16>(),
               "profile slice layout");
@@ -192,58 +194,58 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
                 if (32 + lane < n) sp_next = spill[32 + lane];
             }
             const int steps = n + kWarp - 1;
-            for (int t = 0; t < steps; ++t) {
-                if ((t & 31) == 0 && t > 0) {
-                    sp_cur = sp_next;
-                    if (!first && t + 32 + lane < n) sp_next = spill[t + 32 + lane];
-                }
+            // Step t: lane l updates column t - l.  `checked` steps skip lanes whose column is
+            // outside [0, n); blocks of 32 steps in which every lane's column is inside skip the
+            // test.  Lane 0 takes the previous pass's row of column t from lane (t mod 32) of
+            // sp_cur, which holds columns [32 k, 32 k + 32) during steps [32 k, 32 k + 32).
+            auto step = [&](const int t, const int src, auto checked) {
                 const int up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                 const int up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
-                const int src = t & 31;
                 const int l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
                 const int l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
                 const int j = t - lane;
-                if (j >= 0 && j < n) {
-                    int F = lane == 0 ? l0_f : up_f;                 // F(r0, j)
-                    int d = hm_prev;                                 // (H - Goe)(r0 - 1, j - 1)
-                    hm_prev = lane == 0 ? l0_hm : up_hm;             // (H - Goe)(r0 - 1, j)
-                    const int32_t* prow1 = s_prof + subj[j] * kPStride + my_chunk;
-                    if constexpr (kTB % 2 == 1) {
+                if (decltype(checked)::value && !(j >= 0 && j < n)) return;
+                int F = lane == 0 ? l0_f : up_f;                 // F(r0, j)
+                int d = hm_prev;                                 // (H - Goe)(r0 - 1, j - 1)
+                hm_prev = lane == 0 ? l0_hm : up_hm;             // (H - Goe)(r0 - 1, j)
+                const int32_t* prow1 = s_prof + subj[j] * kPStride + my_chunk;
+                if constexpr (kTB % 2 == 1) {
 #pragma unroll
-                        for (int r = 0; r + 1 < kTB; r += 2) {
-                            const int x0 = cell_i32(d, Hm[r], E[r], F, prow1[r], goe, ge, gep);
-                            const int x1 = cell_i32(d, Hm[r + 1], E[r + 1], F, prow1[r + 1], goe, ge, gep);
-                            best = __vimax3_s32(best, x0, x1);
-                        }
-                        best = max(best, cell_i32(d, Hm[kTB - 1], E[kTB - 1], F, prow1[kTB - 1], goe, ge, gep));
-                    } else {
+                    for (int r = 0; r + 1 < kTB; r += 2) {
+                        const int x0 = cell_i32(d, Hm[r], E[r], F, prow1[r], goe, ge, gep);
+                        const int x1 = cell_i32(d, Hm[r + 1], E[r + 1], F, prow1[r + 1], goe, ge, gep);
+                        best = __vimax3_s32(best, x0, x1);
+                    }
+                    best = max(best, cell_i32(d, Hm[kTB - 1], E[kTB - 1], F, prow1[kTB - 1], goe, ge, gep));
+                } else {
                     const int4* prow = reinterpret_cast<const int4*>(prow1);
 #pragma unroll
                     for (int r4 = 0; r4 < kTB; r4 += 4) {
                         const int4 sv = prow[r4 >> 2];
-                        const int sc[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                        for (int h = 0; h < 4; h += 2) {
-                            const int r = r4 + h;
-                            const int x0 = __viaddmax_s32_relu(d, sc[h], E[r]);
-                            const int xm0 = x0 - goe;
-                            d = Hm[r];
-                            Hm[r] = __viaddmax_s32(F, -goe, xm0);
-                            E[r] = __viaddmax_s32(E[r], -ge, Hm[r]);
-                            F = __viaddmax_s32(F, -gep, xm0);
-                            const int x1 = __viaddmax_s32_relu(d, sc[h + 1], E[r + 1]);
-                            const int xm1 = x1 - goe;
-                            d = Hm[r + 1];
-                            Hm[r + 1] = __viaddmax_s32(F, -goe, xm1);
-                            E[r + 1] = __viaddmax_s32(E[r + 1], -ge, Hm[r + 1]);
-                            F = __viaddmax_s32(F, -gep, xm1);
-                            best = __vimax3_s32(best, x0, x1);
-                        }
+                        const int x0 = cell_i32(d, Hm[r4], E[r4], F, sv.x, goe, ge, gep);
+                        const int x1 = cell_i32(d, Hm[r4 + 1], E[r4 + 1], F, sv.y, goe, ge, gep);
+                        best = __vimax3_s32(best, x0, x1);
+                        const int x2 = cell_i32(d, Hm[r4 + 2], E[r4 + 2], F, sv.z, goe, ge, gep);
+                        const int x3 = cell_i32(d, Hm[r4 + 3], E[r4 + 3], F, sv.w, goe, ge, gep);
+                        best = __vimax3_s32(best, x2, x3);
                     }
-                    }
-                    out_hm = Hm[kTB - 1];
-                    out_f = F;
-                    if (lane == kWarp - 1 && !last) spill[j] = make_int2(out_hm, out_f);
+                }
+                out_hm = Hm[kTB - 1];
+                out_f = F;
+                if (lane == kWarp - 1 && !last) spill[j] = make_int2(out_hm, out_f);
+            };
+            for (int tb = 0; tb < steps; tb += kWarp) {
+                if (tb > 0) {
+                    sp_cur = sp_next;
+                    if (!first && tb + 32 + lane < n) sp_next = spill[tb + 32 + lane];
+                }
+                if (tb >= kWarp && tb + kWarp <= n) {
+#pragma unroll 1
+                    for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{});
+                } else {
+                    const int ue = min(kWarp, steps - tb);
+#pragma unroll 1
+                    for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{});
                 }
             }
             __syncwarp();   // lane 31's spill writes are visible to the warp's next pass
