@@ -373,14 +373,23 @@ def run_ours(args, world, rank, local):
 
         plain_step()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plain_step()
-        e1.record(stream)
+        # one event per query boundary: the pass's total and each query's own time
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nq + 1)]
+        evs[0].record(stream)
+        for k, (dq, o) in enumerate(zip(d_qs, offs1)):
+            sw.sw_search_batch_device(db, dq, o, wl.matrix, wl.gap_open, wl.gap_extend, d_s1,
+                                      stream=stream)
+            evs[k + 1].record(stream)
         torch.cuda.synchronize()
-        p_ms = e0.elapsed_time(e1)
+        p_ms = evs[0].elapsed_time(evs[-1])
+        per_len = []
+        for k, q in enumerate(wl.queries):
+            q_ms = evs[k].elapsed_time(evs[k + 1])
+            per_len.append({"m": len(q), "ms": round(q_ms, 3),
+                            "gcups": round(len(q) * wl.db.num_residues / (q_ms * 1e-3) / 1e9, 1)})
         plain = {"gcups": cells / (p_ms * 1e-3) / 1e9, "ms_per_pass": p_ms,
-                 "what": "the same queries, one per launch (single-query kernel)"}
+                 "what": "the same queries, one per launch (single-query kernel)",
+                 "per_query_length": per_len}
 
     if rank != 0:
         if dist is not None:

@@ -4,10 +4,10 @@
 // query rows and updates column t - l at step t; rows pass between lanes by __shfl_up_sync;
 // a per-warp global buffer carries the bottom row to the next pass) but for the work sources
 // where neighbouring pairs share the query -- subjects above the inter-task cutoff and groups
-// routed off the inter-task kernel -- the four warps of a block take the same query against
-// four neighbouring subjects (longest first), so one copy of the pass's profile slice serves
-// the block.  The slice is stored as int32 (sign-extended and biased once per pass, not once
-// per cell) and each lane owns 16 rows, halving the per-step shuffles and loads per cell.
+// routed off the inter-task kernel -- the warps of a block (8 with 16 rows per lane, else 4)
+// take the same query against as many neighbouring subjects (longest first), so one copy of
+// the pass's profile slice serves the block.  The slice is stored as int32 (sign-extended and
+// biased once per pass, not once per cell) and each lane owns 5, 8 or 16 rows.
 // Eqs. sw2-sw4, Section 2; the intra-task scheme of Section 1.
 //
 // Shared-memory layout of the slice: the 32 lanes read the rows of 32 different residues in
@@ -27,15 +27,15 @@ namespace swgb {
 
 namespace {
 
-constexpr int kBW = 4;                       // warps per block = subjects per block item
-constexpr int kBBlock = kBW * kWarp;
+constexpr int kMaxBW = 8;                   // warps per block = subjects per block item
 
 struct BlockItem {
     int q;
-    int seq[kBW];
+    int seq[kMaxBW];
 };
 
 // Decodes block item `it` (longest subjects first); seq = -1 for absent / filler slots.
+template <int kBW>
 __device__ bool decode_item(const IntraParams& p, unsigned long long it, BlockItem& out) {
     if (p.mode == kIntraLong) {
         const int64_t per_q = (p.num_long + kBW - 1) / kBW;
@@ -130,9 +130,10 @@ __device__ __forceinline__ int cell_i32(int& d, int& hm, int& e, int& f, int sc,
     return x;
 }
 
-// kTB query rows per lane: passes of 32 * kTB rows (160, 256 or 512).
-template <int kTB>
-__global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p) {
+// kTB query rows per lane: passes of 32 * kTB rows (160, 256 or 512); kBW warps per block.
+template <int kTB, int kBW>
+__global__ void __launch_bounds__(kBW * kWarp) k_intra_block_i32(const IntraParams p) {
+    constexpr int kBBlock = kBW * kWarp;
     constexpr int kRowsB = kTB * kWarp;
     constexpr int kPStride = slice_stride<kTB>();   // int32 per shared-memory profile row
     extern __shared__ __align__(16) int32_t s_prof[];     // (A+1) x kPStride
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long it = atomicAdd(counter, 1ull);
-            s_done = decode_item(p, it, s_item) ? 0 : 1;
+            s_done = decode_item<kBW>(p, it, s_item) ? 0 : 1;
             if (!s_done) s_passes = (p.queries[s_item.q].m + kRowsB - 1) / kRowsB;
         }
         __syncthreads();
@@ -258,13 +259,17 @@ __global__ void __launch_bounds__(kBBlock) k_intra_block_i32(const IntraParams p
 
 }  // namespace
 
+// Warps per block: 8 with 16 rows per lane (three 54 KB blocks, 24 warps per SM; four 4-warp
+// blocks gave 16 warps per SM and 5 % less throughput on long subjects), else 4.
+int intra_block_warps(int rows_per_lane) { return rows_per_lane == 16 ? 8 : 4; }
+
 namespace {
 
 const void* block_fn(int rows_per_lane) {
     switch (rows_per_lane) {
-        case 5: return reinterpret_cast<const void*>(&k_intra_block_i32<5>);
-        case 8: return reinterpret_cast<const void*>(&k_intra_block_i32<8>);
-        default: return reinterpret_cast<const void*>(&k_intra_block_i32<16>);
+        case 5: return reinterpret_cast<const void*>(&k_intra_block_i32<5, 4>);
+        case 8: return reinterpret_cast<const void*>(&k_intra_block_i32<8, 4>);
+        default: return reinterpret_cast<const void*>(&k_intra_block_i32<16, 8>);
     }
 }
 
@@ -282,7 +287,9 @@ int intra_block_occupancy(int rows_per_lane, int alphabet1) {
     const size_t smem = intra_block_smem_bytes(rows_per_lane, alphabet1);
     const void* fn = block_fn(rows_per_lane);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBBlock, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, intra_block_warps(rows_per_lane) * kWarp,
+                                                      smem) != cudaSuccess)
+        return 0;
     return n;
 }
 
@@ -295,11 +302,11 @@ cudaError_t launch_intra_block(const IntraParams& p, int rows_per_lane, int grid
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     if (rows_per_lane == 5)
-        k_intra_block_i32<5><<<grid, kBBlock, smem, st>>>(p);
+        k_intra_block_i32<5, 4><<<grid, 4 * kWarp, smem, st>>>(p);
     else if (rows_per_lane == 8)
-        k_intra_block_i32<8><<<grid, kBBlock, smem, st>>>(p);
+        k_intra_block_i32<8, 4><<<grid, 4 * kWarp, smem, st>>>(p);
     else
-        k_intra_block_i32<16><<<grid, kBBlock, smem, st>>>(p);
+        k_intra_block_i32<16, 8><<<grid, 8 * kWarp, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -307,22 +307,27 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     }
     // the block variant shares the per-warp pass buffers: never more blocks than the generic grid
     {
-        // With few block items (a small database), the search ends with the longest subjects'
-        // warps, each sharing its SM sub-partition with the other resident warps; at most three
-        // blocks per SM (three warps per sub-partition) shortens that tail more than it costs in
-        // latency hiding (measured: 10,000 sequences 0.38 -> 0.33 ms; a 50,000 x 20,000-residue
-        // database keeps four blocks per SM, which is 8 % faster there).
+        // With few block items (a small database searched by a short query), the search ends
+        // with the longest subjects' warps, each sharing its SM sub-partition with the other
+        // resident warps; at most three 4-warp blocks per SM (three warps per sub-partition)
+        // shortens that tail more than it costs in latency hiding (measured: 144 residues vs
+        // 10,000 sequences 0.38 -> 0.33 ms).  The 8-warp blocks of long queries keep every block
+        // that fits (one per SM ran 1,000 residues vs 10,000 long subjects 12 % slower).
         int per_sm = db->intra_block_occ[tb_index];
+        const int bw = intra_block_warps(P.intra_rows_per_lane);
         const int64_t n_subjects = static_cast<int64_t>(db->layout.long_ids.size()) +
                                    static_cast<int64_t>(G - P.g_split) * kGroupSeqs;
-        const int64_t block_items = (n_subjects + 3) / 4 * nq;
-        if (block_items < 8LL * db->sms * per_sm) per_sm = std::min(per_sm, 3);
+        const int64_t block_items = (n_subjects + bw - 1) / bw * nq;
+        if (bw == 4 && block_items < 8LL * db->sms * per_sm) per_sm = std::min(per_sm, 3);
         const int forced = forced_intra_blocks_per_sm();
         if (forced > 0) per_sm = std::min(db->intra_block_occ[tb_index], forced);
-        P.intra_block_grid = std::min(P.intra_grid, db->sms * per_sm);
+        P.intra_block_grid = db->sms * per_sm;
+        P.intra_block_warps = bw;
     }
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
-    const int64_t intra_slots = static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp);
+    // per-warp pass buffers, shared by the generic and the block kernel
+    const int64_t intra_slots = std::max<int64_t>(static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp),
+                                                  static_cast<int64_t>(P.intra_block_grid) * P.intra_block_warps);
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
     const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
     P.flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));

@@ -63,6 +63,7 @@ struct Plan {
     int64_t num_items = 0;
     int inter_grid = 0, intra_grid = 0, intra_block_grid = 0;
     int intra_rows_per_lane = 16;
+    int intra_block_warps = 4;
     uint32_t flag_cap = 0;
     int64_t cells = 0, inter_cells = 0, launches = 0;
     DevBuf<int16_t> qp;

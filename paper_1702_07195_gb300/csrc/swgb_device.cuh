@@ -194,6 +194,7 @@ cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t
 // Query rows per lane of the block int32 kernel's variants (passes of 160, 256 and 512 rows).
 constexpr int kIntraBlockRows[3] = {5, 8, 16};
 size_t intra_block_smem_bytes(int rows_per_lane, int alphabet1);
+int intra_block_warps(int rows_per_lane);
 int intra_block_occupancy(int rows_per_lane, int alphabet1);
 cudaError_t launch_intra_block(const IntraParams& p, int rows_per_lane, int grid, cudaStream_t st);
 int intra_block_threads();
