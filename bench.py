@@ -73,6 +73,8 @@ def parse():
                     help="force an inter-task kernel variant instead of autotuning (profiling)")
     ap.add_argument("--placement", default="device", choices=["device", "host"],
                     help="database in HBM (default) or streamed from pinned host memory")
+    ap.add_argument("--score-profile", action="store_true",
+                    help="also time the one-query-per-launch pass with the score-profile kernel")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-query-per-launch comparison")
     return ap.parse_args()
@@ -390,6 +392,21 @@ def run_ours(args, world, rank, local):
         plain = {"gcups": cells / (p_ms * 1e-3) / 1e9, "ms_per_pass": p_ms,
                  "what": "the same queries, one per launch (single-query kernel)",
                  "per_query_length": per_len}
+        if args.score_profile:
+            # the same pass with the score profile (Section 4.3) in place of the query profile
+            os.environ["SWGB_SCORE_PROFILE"] = "1"
+            plain_step()
+            torch.cuda.synchronize()
+            sp_used = sw.sw_get_stats(db)["score_profile"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            del os.environ["SWGB_SCORE_PROFILE"]
+            sp_ms = e0.elapsed_time(e1)
+            plain["score_profile"] = {"gcups": cells / (sp_ms * 1e-3) / 1e9, "ms_per_pass": sp_ms,
+                                      "kernel_used": bool(sp_used)}
 
     if rank != 0:
         if dist is not None:

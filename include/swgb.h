@@ -85,7 +85,8 @@ typedef struct {
     int32_t graph_replay;  /* 1 if the launch sequence was a replayed CUDA graph */
     int32_t variant;       /* inter-task kernel variant used (see sw_db_tune) */
     int32_t multi_query;   /* 1 if two queries shared each register (two or more queries) */
-    int32_t reserved;
+    int32_t score_profile; /* 1 if the single-query inter-task kernel used a score profile
+                              (Section 4.3; environment SWGB_SCORE_PROFILE=1) */
 } sw_stats;
 
 /* ---------------------------------------------------------------- database ------------ */

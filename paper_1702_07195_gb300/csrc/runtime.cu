@@ -67,6 +67,12 @@ bool mq_enabled() {
     return !(v && v[0] == '0');
 }
 
+// Score profile instead of query profile in the single-query inter-task kernel.
+bool score_profile_enabled() {
+    const char* v = std::getenv("SWGB_SCORE_PROFILE");
+    return v && v[0] == '1';
+}
+
 // Blocks per SM of the block int32 kernel (0: as many as fit).
 int forced_intra_blocks_per_sm() {
     const char* v = std::getenv("SWGB_INTRA_BLOCKS_PER_SM");
@@ -148,8 +154,15 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         return P.m[static_cast<size_t>(a)] > P.m[static_cast<size_t>(b)];
     });
 
+    int nonempty = 0;
+    for (int q = 0; q < nq; ++q) nonempty += P.m[static_cast<size_t>(q)] > 0;
+    // Score-profile kernel (single-query launches only; 32 rows per strip, 4 warps per block).
+    P.sp = score_profile_enabled() && P.int16_ok && !(mq_enabled() && nonempty >= 2) &&
+           db->inter_sp_occ > 0;
+    if (P.sp) P.variant = 0;
+
     // Work items of the inter-task kernel: (query, W consecutive groups), largest first.
-    const int W = inter_variant_warps(P.variant);
+    const int W = P.sp ? inter_sp_warps() : inter_variant_warps(P.variant);
     std::vector<InterItem> items;
     const int64_t G = db->layout.num_groups;
     if (P.int16_ok && G > 0) {
@@ -179,8 +192,6 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
 
     // Two or more queries: pair them two per register (multi-query kernel).  Queries go, strip
     // by strip, into two streams balanced by strip count, longest first.
-    int nonempty = 0;
-    for (int q = 0; q < nq; ++q) nonempty += P.m[static_cast<size_t>(q)] > 0;
     std::vector<MqStep> steps;
     const int mqT = inter_mq_variant_rows(P.variant);
     P.mq = mq_enabled() && P.int16_ok && G > 0 && nonempty >= 2 &&
@@ -285,7 +296,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     if (P.g_split == 0) P.mq = false;
 
     // Scratch shared by all plans of this database.
-    P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]);
+    P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant]
+                                              : P.sp ? db->inter_sp_occ : db->inter_occ[P.variant]);
     P.intra_grid = db->sms * std::max(1, db->intra_occ);
     // Rows per lane of the block int32 kernel: the fewer padded rows (with a per-step overhead
     // of about 10 operations per lane against 5.5 per cell) the better.
@@ -344,6 +356,15 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     CU(P.qoff.ensure(static_cast<size_t>(nq) + 1));
     CU(P.order.ensure(static_cast<size_t>(nq)));
     CU(P.matrix.ensure(static_cast<size_t>(A * A)));
+    std::vector<int16_t> mt;
+    if (P.sp) {   // transposed biased matrix: mt[s][a] = SM(a, s) + bias, the dummy letter scores 0
+        const int ms = inter_sp_mt_stride();
+        mt.assign(static_cast<size_t>((A + 1) * ms), static_cast<int16_t>(P.qp_bias));
+        for (int sl = 0; sl < A; ++sl)
+            for (int a = 0; a < A; ++a)
+                mt[static_cast<size_t>(sl * ms + a)] = static_cast<int16_t>(h_matrix[a * A + sl] + P.qp_bias);
+        CU(P.mt.ensure(mt.size()));
+    }
     if (P.mq) {
         CU(P.steps.ensure(steps.size()));
         CU(P.pp.ensure(static_cast<size_t>((A + 1) * P.rows_pad)));
@@ -366,6 +387,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     if (P.mq)
         CU(cudaMemcpyAsync(P.steps.ptr, steps.data(), sizeof(MqStep) * steps.size(),
                            cudaMemcpyHostToDevice, us));
+    if (P.sp)
+        CU(cudaMemcpyAsync(P.mt.ptr, mt.data(), sizeof(int16_t) * mt.size(), cudaMemcpyHostToDevice, us));
     CU(cudaStreamSynchronize(us));
 
     const Gaps gaps{goe, ge, std::min(goe, ge)};
@@ -385,6 +408,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     ip.bnd = db->bnd.ptr;
     ip.bnd_stride = bnd_stride;
     ip.gaps = gaps;
+    ip.qres_off = P.qoff.ptr;
+    ip.mt = P.sp ? P.mt.ptr : nullptr;
     if (P.mq) {
         InterMqParams& mp = P.inter_mq;
         mp.inter = db->inter_ptr;
@@ -476,7 +501,13 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
         CU(launch_inter_mq(P.inter_mq, P.variant, P.inter_grid, st));
         launches += 2;
     } else if (P.num_items > 0) {
-        CU(launch_inter(P.inter, P.variant, P.inter_grid, st));
+        if (P.sp) {
+            InterParams ip = P.inter;
+            ip.qres = d_queries;
+            CU(launch_inter_sp(ip, P.inter_grid, st));
+        } else {
+            CU(launch_inter(P.inter, P.variant, P.inter_grid, st));
+        }
         ++launches;
     }
     CU(record(db->ev[2], st));
@@ -550,6 +581,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(forced_split());
     key.push_back(db->no_route ? 1 : 0);
     key.push_back(forced_intra_blocks_per_sm());
+    key.push_back(score_profile_enabled() ? 1 : 0);
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 
@@ -599,6 +631,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     db->stats.inter_grid = plan->inter_grid;
     db->stats.inter_block = inter_variant_warps(plan->variant) * kWarp;
     db->stats.multi_query = plan->mq ? 1 : 0;
+    db->stats.score_profile = plan->sp && plan->num_items > 0 ? 1 : 0;
     db->stats.graph_replay = replay ? 1 : 0;
     db->stats.variant = plan->variant;
     db->stats_pending = true;
@@ -733,6 +766,7 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     for (int v = 0; v < inter_mq_num_variants() && v < kMaxVariants; ++v)
         db->inter_mq_occ[v] = inter_mq_occupancy(v, alphabet_size + 1);
     db->intra_occ = intra_occupancy(alphabet_size + 1);
+    db->inter_sp_occ = inter_sp_occupancy(alphabet_size + 1);
     const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
     for (int v = 0; v < 3; ++v)
         db->intra_block_occ[v] = block_off ? 0 : intra_block_occupancy(kIntraBlockRows[v], alphabet_size + 1);

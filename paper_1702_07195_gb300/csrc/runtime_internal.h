@@ -79,6 +79,8 @@ struct Plan {
     int64_t g_split = 0;      // groups [g_split, G) run on the int32 kernel (critical path)
     // multi-query kernel (two queries per register against one subject)
     bool mq = false;
+    bool sp = false;              // score-profile single-query kernel
+    DevBuf<int16_t> mt;           // its transposed biased matrix
     int32_t num_steps = 0;
     int64_t rows_pad = 0;
     DevBuf<MqStep> steps;
@@ -130,6 +132,7 @@ struct sw_db {
     int inter_mq_occ[swgb::kMaxVariants] = {};
     int intra_occ = 0;
     int intra_block_occ[3] = {0, 0, 0};   // 5, 8 and 16 query rows per lane
+    int inter_sp_occ = 0;                 // score-profile inter-task kernel
     // last search
     sw_stats stats{};
     bool stats_pending = false;

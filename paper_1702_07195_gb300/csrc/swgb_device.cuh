@@ -96,6 +96,10 @@ struct InterParams {
     Gaps gaps;
     const TickDesc* tick;   // non-null: items come from this tick descriptor, not `items`
     int32_t num_groups;     // groups in the database (tick mode)
+    // score-profile kernel only: query residues, their offsets, the biased transposed matrix
+    const uint8_t* qres;
+    const int64_t* qres_off;
+    const int16_t* mt;      // mt[s * inter_sp_mt_stride() + a] = SM(a, s) + bias
 };
 
 // Multi-query inter-task kernel: the two int16 lanes of a register hold two different queries
@@ -175,6 +179,12 @@ int inter_variant_warps(int variant);
 size_t inter_smem_bytes(int alphabet1);
 int inter_occupancy(int variant, int alphabet1);
 cudaError_t launch_inter(const InterParams& p, int variant, int grid, cudaStream_t st);
+// Score-profile form of the single-query inter-task kernel (32 rows per strip, 4 warps).
+int inter_sp_mt_stride();
+int inter_sp_warps();
+size_t inter_sp_smem_bytes(int alphabet1);
+int inter_sp_occupancy(int alphabet1);
+cudaError_t launch_inter_sp(const InterParams& p, int grid, cudaStream_t st);
 int inter_mq_num_variants();
 int inter_mq_variant_rows(int variant);
 int inter_mq_variant_warps(int variant);
