@@ -325,7 +325,13 @@ def run_ours(args, world, rank, local):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = world * cells / (t_max * 1e-3) / 1e9
+    # units all ranks processed (each rank's database has its own seed, so sizes differ slightly)
+    cells_all = cells
+    if dist is not None:
+        c = torch.tensor([cells], dtype=torch.int64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        cells_all = int(c.item())
+    value = cells_all / (t_max * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -357,7 +363,7 @@ def run_ours(args, world, rank, local):
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": world * cells / dt / 1e9, "unit": "GCUPS",
+        e2e = {"value": cells_all / dt / 1e9, "unit": "GCUPS",
                "h2d_bytes_per_step": int(cat.size + mat.size),
                "d2h_bytes_per_step": int(nq * N * 4)}
 
@@ -454,6 +460,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD_TEXT[args.workload], "queries": nq,
                        "query_residues": int(cat.size), "db_seqs": N,
                        "db_residues": wl.db.num_residues, "cells_per_step": cells,
+                       "cells_per_step_all_ranks": cells_all,
                        "kernel_variant": tune,
                        "per_gpu": "each rank searches its own database of this size",
                        "placement": args.placement,
