@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain", "paper_shaped", "long_subject", "serving"])
+                    choices=["batched", "plain", "paper_shaped", "long_subject", "serving",
+                             "simd_rates"])
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
     ap.add_argument("--rates", default="0.25,0.5,0.9,1.1",
                     help="serving: arrival rates as fractions of the measured capacity")
@@ -544,11 +545,39 @@ def run_serving(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_simd_rates(args, rank):
+    """The int8-tier study (Section 4.2's 8-bit first tier): rates of the packed-integer
+    operations a cell update can be built from, measured by the probe that build() compiles,
+    and the cell-update rates they bound (int16x2 DPX vs 4 x 8-bit SIMD)."""
+    if rank != 0:
+        return
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_swgb_build", os.path.join(ROOT, "paper_1702_07195_gb300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    b.build()
+    r = subprocess.run([b.PROBE], capture_output=True, text=True, timeout=300)
+    probe = json.loads(r.stdout.strip().splitlines()[-1])
+    if r.returncode != 0 or "error" in probe:
+        raise RuntimeError(f"probe failed: {r.stdout} {r.stderr}")
+    cu = probe["cell_updates_per_s"]
+    print(json.dumps({"metric": "cell-update rate bound from packed-integer operation rates",
+                      "value": cu["int16x2_dpx"] / 1e9, "unit": "GCUPS", "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "int16x2 vs int8x4", "data": "synthetic",
+                      "config": {"workload": "simd_rates"},
+                      "int8x4_simd_gcups_bound": cu["int8x4_simd"] / 1e9,
+                      "int16x2_over_int8x4": cu["int16x2_dpx"] / cu["int8x4_simd"],
+                      "probe": probe}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "simd_rates":
+        run_simd_rates(args, rank)
     elif args.workload == "serving":
         run_serving(args, world, rank, local)
     else:
