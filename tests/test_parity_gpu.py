@@ -308,6 +308,27 @@ def test_group_routing_to_intra_kernel(sw, split, monkeypatch):
         assert st1["intra_ms"] > 0      # a small database routes its long groups
 
 
+def test_routed_groups_pass_heights(sw, monkeypatch):
+    """Every group routed (split 0) to the int32 block kernel: the oracle's scores for query
+    lengths around its 160-, 256- and 512-row passes (5, 8 and 16 rows per lane), odd subject
+    counts (a part-filled last block item) and empty sequences."""
+    monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
+    rng = np.random.default_rng(91)
+    lens = np.concatenate([rng.integers(1, 700, size=203), [0, 0, 1, 2, 33]])
+    db = w.database_from_lengths(rng, lens)
+    sm = w.blosum62()
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        for m in (1, 31, 159, 160, 161, 255, 256, 257, 511, 512, 600):
+            q = w.draw_residues(rng, m)
+            got = sw.sw_search(h, q, sm, 10, 2)
+            st = sw.sw_get_stats(h)
+            _check(got[None], _oracle_all([q], db, sm, 10, 2), f"m={m}")
+            assert st["inter_cells"] == 0 and st["intra_ms"] > 0
+        qs = [w.draw_residues(rng, 90), w.draw_residues(rng, 200)]
+        got = sw.sw_search_batch(h, qs, sm, 3, 7)
+    _check(got, _oracle_all(qs, db, sm, 3, 7), "batch, gaps 3/7")
+
+
 @pytest.mark.parametrize("k", [1, 5, 64, 1000, 4096])
 def test_sorting_stage_topk(sw, k):
     """Sorting stage: device top-k equals a full sort by (descending score, ascending index)
