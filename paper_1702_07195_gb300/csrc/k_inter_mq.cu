@@ -73,36 +73,36 @@ __device__ __forceinline__ void strip_mq(const uint4* __restrict__ res, int L, i
     const unsigned init_f = k.ngep, init_hm = k.ngoe;
     const uint4 init = make_uint4(init_hm, init_f, init_hm, init_f);
     unsigned hm_prev = k.ngoe;
-    const int shift = 8 * h;
     uint4 w_next = res[lane];
-    uint4 b_next = read ? bnd[lane] : init;
+    // boundary records alternate between two registers sets (no copy per record)
+    uint4 b_a = read ? bnd[lane] : init, b_b = init;
+    // Columns j, j + 1: residues are bytes h and 2 + h of word wq; b holds the previous strip's
+    // record of these columns, b_pref receives the next record.
+    auto two_columns = [&](const unsigned wq, uint4 b, uint4& b_pref, const int j) {
+        if (read && j + 2 < L) b_pref = bnd[((j >> 1) + 1) * kWarp + lane];
+        if (keep != 0xFFFFFFFFu) {
+            b.x = (b.x & keep) | (init.x & ~keep);
+            b.y = (b.y & keep) | (init.y & ~keep);
+            b.z = (b.z & keep) | (init.z & ~keep);
+            b.w = (b.w & keep) | (init.w & ~keep);
+        }
+        const unsigned c0 = __byte_perm(wq, 0u, 0x4440u + h);
+        const unsigned c1 = __byte_perm(wq, 0u, 0x4442u + h);
+        unsigned f0 = b.y;
+        column_mq<kT>(Hm, E, f0, hm_prev, pp_strip + c0 * pstride, k, best);
+        const unsigned out_hm0 = Hm[kT - 1];
+        unsigned f1 = b.w;
+        column_mq<kT>(Hm, E, f1, b.x, pp_strip + c1 * pstride, k, best);
+        hm_prev = b.z;
+        if (write) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
+    };
     for (int jc = 0; jc < L; jc += 8) {
         const uint4 w = w_next;
         if (jc + 8 < L) w_next = res[((jc >> 3) + 1) * kWarp + lane];
-        unsigned w0 = w.x, w1 = w.y, w2 = w.z, w3 = w.w;
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int j = jc + 2 * q;
-            uint4 b = b_next;
-            if (read && j + 2 < L) b_next = bnd[((j >> 1) + 1) * kWarp + lane];
-            if (keep != 0xFFFFFFFFu) {
-                b.x = (b.x & keep) | (init.x & ~keep);
-                b.y = (b.y & keep) | (init.y & ~keep);
-                b.z = (b.z & keep) | (init.z & ~keep);
-                b.w = (b.w & keep) | (init.w & ~keep);
-            }
-            const unsigned c0 = (w0 >> shift) & 0xFFu;
-            const unsigned c1 = (w0 >> (16 + shift)) & 0xFFu;
-            unsigned f0 = b.y;
-            column_mq<kT>(Hm, E, f0, hm_prev, pp_strip + c0 * pstride, k, best);
-            const unsigned out_hm0 = Hm[kT - 1];
-            unsigned f1 = b.w;
-            column_mq<kT>(Hm, E, f1, b.x, pp_strip + c1 * pstride, k, best);
-            hm_prev = b.z;
-            if (write) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
-            w0 = w1;
-            w1 = w2;
-            w2 = w3;
+        for (int q2 = 0; q2 < 2; ++q2) {
+            two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
+            two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
         }
     }
 }
