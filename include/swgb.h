@@ -28,6 +28,13 @@
  *  - On a non-OK status no output is defined; sw_last_error() says why (thread-local).
  *  - Host input buffers are borrowed for the duration of the call only.
  *  - Calls on one database handle are serialised internally.
+ *
+ * Environment switches (experiments; the defaults are the measured best): SWGB_MQ=0 (no
+ * two-queries-per-register kernel), SWGB_VARIANT=v (force an inter-task variant, read at
+ * load), SWGB_GROUP_SPLIT=s (groups [0, s) on the inter-task kernel, the rest on the int32
+ * intra-task kernel), SWGB_INTRA_BLOCK=0 (per-warp int32 kernel, read at load),
+ * SWGB_INTRA_BLOCKS_PER_SM=n, SWGB_SCORE_PROFILE=1 (score-profile single-query kernel,
+ * Section 4.3), SWGB_GRAPHS=0 (no CUDA-graph capture).  Scores do not depend on them.
  */
 #ifndef SWGB_H
 #define SWGB_H
@@ -73,7 +80,7 @@ typedef struct {
 /* Per-call measurements of the last search on a handle (CUDA events on the launch stream). */
 typedef struct {
     float inter_ms;        /* inter-task int16x2 kernel */
-    float intra_ms;        /* intra-task int32 kernel for long subjects */
+    float intra_ms;        /* intra-task int32 kernel (long subjects, routed groups) */
     float rescore_ms;      /* int32 rescore of saturated lanes */
     float total_ms;        /* first to last launch of the search */
     int64_t cells;         /* sum over queries of m * (database residues) */
