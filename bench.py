@@ -371,6 +371,12 @@ def run_ours(args, world, rank, local):
     # the same queries, one query per launch (the "plain" search): same kernels, no batching
     plain = None
     if not args.no_plain and nq > 1:
+        # the single-query kernel gets its own tuned variant (the batch run's variant was tuned
+        # for the two-queries-per-register kernel); restored after the comparison
+        plain_variant = None
+        if args.variant < 0 and not args.no_tune:
+            med = sorted(wl.queries, key=len)[len(wl.queries) // 2]
+            plain_variant = sw.sw_db_tune(db, [med], wl.matrix, wl.gap_open, wl.gap_extend)
         offs1 = [np.array([0, len(q)], np.int64) for q in wl.queries]
         d_qs = [torch.from_numpy(q).cuda() for q in wl.queries]
         d_s1 = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -398,7 +404,7 @@ def run_ours(args, world, rank, local):
                             "gcups": round(len(q) * wl.db.num_residues / (q_ms * 1e-3) / 1e9, 1)})
         plain = {"gcups": cells / (p_ms * 1e-3) / 1e9, "ms_per_pass": p_ms,
                  "what": "the same queries, one per launch (single-query kernel)",
-                 "per_query_length": per_len}
+                 "kernel_variant": plain_variant, "per_query_length": per_len}
         if args.score_profile:
             # the same pass with the score profile (Section 4.3) in place of the query profile
             os.environ["SWGB_SCORE_PROFILE"] = "1"
@@ -414,6 +420,8 @@ def run_ours(args, world, rank, local):
             sp_ms = e0.elapsed_time(e1)
             plain["score_profile"] = {"gcups": cells / (sp_ms * 1e-3) / 1e9, "ms_per_pass": sp_ms,
                                       "kernel_used": bool(sp_used)}
+        if plain_variant is not None and tune is not None:
+            sw.sw_db_set_variant(db, tune["variant"])
 
     if rank != 0:
         if dist is not None:
