@@ -174,9 +174,14 @@ KERNEL_SRC = {"k_inter_i16x2": INTER_SRC,
                                                 "k_intra_block.cu")}
 
 
-def ncu_traffic(workload, kernel=INTER_KERNEL):
+# rows per strip of the inter-task kernel variants (both kernels), as in csrc/k_inter*.cu
+INTER_VARIANT_ROWS = (32, 64, 32, 64)
+
+
+def ncu_traffic(workload, kernel=INTER_KERNEL, rows_per_strip=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
-    if the summary is absent or was taken on a different kernel source."""
+    if the summary is absent, was taken on a different kernel source, or (for the inter-task
+    kernels, whose boundary traffic scales with the strip count) on another strip height."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -185,6 +190,9 @@ def ncu_traffic(workload, kernel=INTER_KERNEL):
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_src or not m_b or m_src.group(1) != src:
+        return None
+    m_rows = re.search(r"rows_per_strip:\s*(\d+)", text)
+    if m_rows and rows_per_strip is not None and int(m_rows.group(1)) != rows_per_strip:
         return None
     return float(m_b.group(1))
 
@@ -452,7 +460,10 @@ def run_ours(args, world, rank, local):
                  "cell pair (ALU-pipe bound; HBM is not the bound)")
     achieved = k_cells / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
-                "frac": achieved / peak_gcups, "traffic": ncu_traffic(args.workload, kernel_name),
+                "frac": achieved / peak_gcups,
+                "traffic": ncu_traffic(args.workload, kernel_name,
+                                       INTER_VARIANT_ROWS[st_last["variant"]]
+                                       if kernel_name.startswith("k_inter") else None),
                 "kernel": kernel_name, "kernel_ms": k_ms, "kernel_cells": int(k_cells),
                 "peak_basis": basis,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks_source": peak_src}
