@@ -308,6 +308,23 @@ def test_group_routing_to_intra_kernel(sw, split, monkeypatch):
         assert st1["intra_ms"] > 0      # a small database routes its long groups
 
 
+def test_very_long_query(sw):
+    """A 20,000-residue query (many strips of the inter-task kernel, 40 passes of the int32
+    kernel) against short and long subjects, alone and batched with a short query."""
+    rng = np.random.default_rng(17)
+    lens = np.concatenate([rng.integers(1, 400, size=150), [5000, 9000]])
+    db = w.database_from_lengths(rng, lens)
+    sm = w.blosum62()
+    q = w.draw_residues(rng, 20000)
+    q2 = w.draw_residues(rng, 50)
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE, long_cutoff=4096) as h:
+        got = sw.sw_search_batch(h, [q, q2], sm, 10, 2)
+        got1 = sw.sw_search(h, q, sm, 10, 2)
+    exp = _oracle_all([q, q2], db, sm, 10, 2)
+    _check(got, exp, "20,000-residue query, batched")
+    _check(got1[None], exp[:1], "20,000-residue query, alone")
+
+
 def test_routed_groups_pass_heights(sw, monkeypatch):
     """Every group routed (split 0) to the int32 block kernel: the oracle's scores for query
     lengths around its 160-, 256- and 512-row passes (5, 8 and 16 rows per lane), odd subject
