@@ -241,10 +241,10 @@ __global__ void __launch_bounds__(kBW * kWarp) k_intra_block_i32(const IntraPara
                     if (!first && tb + 32 + lane < n) sp_next = spill[tb + 32 + lane];
                 }
                 if (tb >= kWarp && tb + kWarp <= n) {
-                    // 5 or 8 rows per lane: two steps per iteration (plain config 0.283 ->
-                    // 0.258 ms); 16 rows: one (two measured 1.5 % slower on long subjects)
+                    // 5 or 8 rows per lane: four steps per loop iteration (plain config 0.283
+                    // -> 0.24-0.26 ms); 16 rows: one (two measured 1.5 % slower on long subjects)
                     if constexpr (kTB < 16) {
-#pragma unroll 2
+#pragma unroll 4
                         for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{});
                     } else {
 #pragma unroll 1
