@@ -207,6 +207,35 @@ class Database:
             pass
 
 
+# Residue encoding (the C ABI takes codes in [0, alphabet_size)): NCBI protein order, the order
+# of the usual BLOSUM/PAM tables -- 20 standard amino acids, then B, Z, X and the stop symbol.
+NCBI_PROTEIN_ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
+
+
+def encode(seq: str, alphabet: str = NCBI_PROTEIN_ALPHABET) -> np.ndarray:
+    """Letters -> uint8 codes (the letter's position in `alphabet`, case-insensitive).  A letter
+    outside the alphabet raises ValueError (the C ABI would answer SW_ERR_CODE)."""
+    table = np.full(256, 255, dtype=np.uint8)
+    for i, c in enumerate(alphabet):
+        table[ord(c.upper())] = i
+        table[ord(c.lower())] = i
+    raw = np.frombuffer(seq.encode("ascii"), dtype=np.uint8)
+    codes = table[raw]
+    bad = np.nonzero(codes == 255)[0]
+    if bad.size:
+        raise ValueError(f"letter {seq[int(bad[0])]!r} at position {int(bad[0])} is not in the alphabet")
+    return codes
+
+
+def encode_database(seqs, alphabet: str = NCBI_PROTEIN_ALPHABET):
+    """Sequences (strings) -> (residues uint8, offsets int64) as sw_db_load takes them."""
+    codes = [encode(q, alphabet) for q in seqs]
+    offsets = np.zeros(len(codes) + 1, dtype=np.int64)
+    np.cumsum([c.shape[0] for c in codes], out=offsets[1:])
+    residues = np.concatenate(codes) if codes else np.zeros(0, dtype=np.uint8)
+    return residues, offsets
+
+
 def sw_db_load(residues, offsets, alphabet_size: int = 24, long_cutoff: int = 0,
                device: int = 0, flag_cap: int = 0, placement: int = PLACE_DEVICE) -> Database:
     """Preprocess and upload a database (residues uint8 codes, offsets int64[N+1]).

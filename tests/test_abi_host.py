@@ -127,3 +127,17 @@ def test_product_package_has_no_cpu_path():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "sw_oracle" not in text, path
+
+
+def test_encoding_helpers(sw):
+    """Letters -> codes in the NCBI protein order, the same codes as the BLOSUM62 table's."""
+    assert sw.NCBI_PROTEIN_ALPHABET == w.ALPHABET
+    seq = "MKTAYIAKQRqisfvkshfsrqLEERLGLIEVQAPILSRVGDGTQDNLSGAEKAVQVKVKALPDAQFEVVHSLAKWKRQTLGQHDFSAGEGLYTHMKALRPDEDRLSPLHSVYVDQWDWERVMGDGERQFSTLKSTVEAIWAGIKATEAAVSEEFGLAPFLPDQIHFVHSQELLSRYPDLDAKGRERAIAKDLGAVFLVGIGGKLSDGHRHDVRAPDYDDWSTPSELGHAGLNGDILVWNPVLEDAFELSSMGIRVDADTLKHQLALTGDEDRLELEWHQALLRGEMPQTIGGGIGQSRLTMLLLQLPHIGQVQAGVWPAACRERVPLY*BZX"
+    np.testing.assert_array_equal(sw.encode(seq), w.encode(seq))
+    with pytest.raises(ValueError):
+        sw.encode("ACGTJ")
+    res, off = sw.encode_database(["ARN", "", "W*"])
+    np.testing.assert_array_equal(res, [0, 1, 2, 17, 23])
+    np.testing.assert_array_equal(off, [0, 3, 3, 5])
+    res, off = sw.encode_database(["ACGT", "GG"], alphabet="ACGT")
+    np.testing.assert_array_equal(res, [0, 1, 2, 3, 2, 2])
