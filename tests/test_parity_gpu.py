@@ -308,6 +308,38 @@ def test_group_routing_to_intra_kernel(sw, split, monkeypatch):
         assert st1["intra_ms"] > 0      # a small database routes its long groups
 
 
+def test_concurrent_searches_on_one_handle(sw):
+    """Four host threads search one database handle at once (calls are serialised inside the
+    library; plans and graphs are shared): every result equals the sequential one."""
+    import threading
+    wl = w.plain(seed=41, scale=0.05)
+    rng = np.random.default_rng(43)
+    qs = [w.draw_residues(rng, int(m)) for m in rng.integers(1, 400, size=16)]
+    with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
+        ref = [sw.sw_search(h, q, wl.matrix, 10, 2) for q in qs]
+        out, errors = [None] * len(qs), []
+
+        def client(ids):
+            try:
+                for i in ids:
+                    out[i] = sw.sw_search(h, qs[i], wl.matrix, 10, 2)
+                    if i % 3 == 0:
+                        b = sw.sw_search_batch(h, [qs[i], qs[(i + 1) % len(qs)]], wl.matrix, 10, 2)
+                        assert np.array_equal(b[0], ref[i]) and np.array_equal(b[1], ref[(i + 1) % len(qs)])
+            except Exception as exc:   # surfaced below
+                errors.append(exc)
+
+        threads = [threading.Thread(target=client, args=(list(range(c, len(qs), 4)),)) for c in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    assert not errors, errors
+    for i in range(len(qs)):
+        assert np.array_equal(out[i], ref[i]), f"query {i}"
+    _check(np.stack(ref[:2]), _oracle_all(qs[:2], wl.db, wl.matrix, 10, 2), "sequential reference")
+
+
 def test_very_long_query(sw):
     """A 20,000-residue query (many strips of the inter-task kernel, 40 passes of the int32
     kernel) against short and long subjects, alone and batched with a short query."""
