@@ -59,6 +59,8 @@ def parse():
                     choices=["batched", "plain", "paper_shaped", "long_subject", "serving",
                              "simd_rates"])
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="serving: database slices per scan cycle (0: automatic)")
     ap.add_argument("--rates", default="0.25,0.5,0.9,1.1",
                     help="serving: arrival rates as fractions of the measured capacity")
     ap.add_argument("--scale", type=float, default=1.0, help="database scale (tests only)")
@@ -511,7 +513,7 @@ def run_serving(args, world, rank, local):
     R = wl.db.num_residues
     probe = w.serving_queries(2, seed=args.seed + 50)
     tune = sw.sw_db_tune(db, probe, wl.matrix, wl.gap_open, wl.gap_extend)
-    srv = sw.Server(db, wl.matrix, wl.gap_open, wl.gap_extend, max_inflight=32, slices=0)
+    srv = sw.Server(db, wl.matrix, wl.gap_open, wl.gap_extend, max_inflight=32, slices=args.slices)
     # capacity: a burst of requests submitted together
     burst = w.serving_queries(48, seed=args.seed + 100)
     for t in [srv.submit(q) for q in burst[:8]]:      # warm-up
@@ -556,7 +558,8 @@ def run_serving(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (int32 rescore)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT["serving"], "db_seqs": wl.db.num_seqs,
-                       "db_residues": R, "max_inflight": 32, "slices": "auto",
+                       "db_residues": R, "max_inflight": 32,
+                       "slices": args.slices if args.slices > 0 else "auto",
                        "kernel_variant": tune,
                        "capacity_rps": capacity, "capacity_gcups": cap_stats["gcups"]},
             "serving": results, "clocks": clocks}
