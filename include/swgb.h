@@ -190,7 +190,9 @@ sw_status sw_topk(const int32_t *d_scores, int64_t num_seqs, int32_t num_queries
  * busy), followed by the int32 work (long subjects of newly admitted
  * requests, saturated lanes).  A request admitted while others run joins at the next tick and
  * completes after one full cycle of slices; its scores (original order) are then copied to the
- * host.  Each score equals the one sw_search returns for the same query.
+ * host.  A request that finds the server idle and nothing pending scans the whole database in
+ * one tick when that tick is short against the recent gaps between submissions.  Each score
+ * equals the one sw_search returns for the same query.
  * Gap costs must fit the int16 path (gap_open, gap_extend <= 16383). */
 typedef struct {
     int32_t max_inflight;        /* requests on the GPU at once (default 32, max 128) */
