@@ -198,12 +198,16 @@ __global__ void __launch_bounds__(kBW * kWarp) k_intra_block_i32(const IntraPara
             // Step t: lane l updates column t - l.  `checked` steps skip lanes whose column is
             // outside [0, n); blocks of 32 steps in which every lane's column is inside skip the
             // test.  Lane 0 takes the previous pass's row of column t from lane (t mod 32) of
-            // sp_cur, which holds columns [32 k, 32 k + 32) during steps [32 k, 32 k + 32).
-            auto step = [&](const int t, const int src, auto checked) {
+            // sp_cur, which holds columns [32 k, 32 k + 32) during steps [32 k, 32 k + 32); in the
+            // first pass that row is the zero boundary, a constant (`on_first`: no shuffle).
+            auto step = [&](const int t, const int src, auto checked, auto on_first) {
                 const int up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                 const int up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
-                const int l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
-                const int l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                int l0_hm = -goe, l0_f = -gep;
+                if constexpr (!decltype(on_first)::value) {
+                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
+                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                }
                 const int j = t - lane;
                 if (decltype(checked)::value && !(j >= 0 && j < n)) return;
                 int F = lane == 0 ? l0_f : up_f;                 // F(r0, j)
@@ -235,27 +239,35 @@ __global__ void __launch_bounds__(kBW * kWarp) k_intra_block_i32(const IntraPara
                 out_f = F;
                 if (lane == kWarp - 1 && !last) spill[j] = make_int2(out_hm, out_f);
             };
-            for (int tb = 0; tb < steps; tb += kWarp) {
-                if (tb > 0) {
-                    sp_cur = sp_next;
-                    if (!first && tb + 32 + lane < n) sp_next = spill[tb + 32 + lane];
-                }
-                if (tb >= kWarp && tb + kWarp <= n) {
-                    // 5 or 8 rows per lane: four steps per loop iteration (plain config 0.283
-                    // -> 0.24-0.26 ms); 16 rows: one (two measured 1.5 % slower on long subjects)
-                    if constexpr (kTB < 16) {
-#pragma unroll 4
-                        for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{});
-                    } else {
-#pragma unroll 1
-                        for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{});
+            auto run = [&](auto on_first) {
+                for (int tb = 0; tb < steps; tb += kWarp) {
+                    if constexpr (!decltype(on_first)::value) {
+                        if (tb > 0) {
+                            sp_cur = sp_next;
+                            if (tb + 32 + lane < n) sp_next = spill[tb + 32 + lane];
+                        }
                     }
-                } else {
-                    const int ue = min(kWarp, steps - tb);
+                    if (tb >= kWarp && tb + kWarp <= n) {
+                        // 5 or 8 rows per lane: four steps per loop iteration (plain config
+                        // 0.283 -> 0.24-0.26 ms); 16 rows: one (two measured 1.5 % slower)
+                        if constexpr (kTB < 16) {
+#pragma unroll 4
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        } else {
 #pragma unroll 1
-                    for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{});
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        }
+                    } else {
+                        const int ue = min(kWarp, steps - tb);
+#pragma unroll 1
+                        for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{}, on_first);
+                    }
                 }
-            }
+            };
+            if (first)
+                run(std::true_type{});
+            else
+                run(std::false_type{});
             __syncwarp();   // lane 31's spill writes are visible to the warp's next pass
         }
 #pragma unroll
