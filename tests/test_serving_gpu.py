@@ -138,3 +138,18 @@ def test_concurrent_clients(sw):
     for k in range(len(qs)):
         assert np.array_equal(out[k], ref[k]), f"request {k}"
     assert st["completed"] == len(qs)
+
+
+def test_only_long_subjects(sw):
+    """A database whose every sequence is above the inter-task cutoff: ticks run only the
+    intra-task work (no interleaved groups), and results still equal the oracle."""
+    rng = np.random.default_rng(29)
+    db = w.database_from_lengths(rng, rng.integers(100, 300, size=20))
+    sm = w.blosum62()
+    qs = w.serving_queries(5, seed=31)
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE, long_cutoff=64) as h:
+        with sw.Server(h, sm, 10, 2, max_inflight=4) as srv:
+            out = [srv.wait(t) for t in [srv.submit(q) for q in qs]]
+    for k, q in enumerate(qs):
+        exp, _ = oracle.sw_search(q, db.residues, db.offsets, sm, 10, 2)
+        assert np.array_equal(out[k].astype(np.int64), exp), f"request {k}"
