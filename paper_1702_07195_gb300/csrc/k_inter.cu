@@ -97,32 +97,32 @@ __device__ __forceinline__ void strip(const uint4* __restrict__ res, int L, uint
     const unsigned f_top = k.ngep;   // F(1, j) = max(0 - Goe, 0 - Ge) on the first strip
     unsigned hm_prev = k.ngoe;       // (H - Goe)(r0 - 1, j - 1), column 0
     uint4 w_next = res[lane];
-    uint4 b_next = first ? make_uint4(k.ngoe, f_top, k.ngoe, f_top) : bnd[lane];
+    // boundary records alternate between two register sets (no copy per record)
+    uint4 b_a = first ? make_uint4(k.ngoe, f_top, k.ngoe, f_top) : bnd[lane];
+    uint4 b_b = b_a;
+    // Columns j and j + 1: residue bytes of word wq (lane a, lane b per column); b holds the
+    // previous strip's record of these columns, b_pref receives the next record.
+    auto two_columns = [&](const unsigned wq, const uint4 b, uint4& b_pref, const int j) {
+        if (!first && j + 2 < L) b_pref = bnd[((j >> 1) + 1) * kWarp + lane];
+        unsigned f0 = b.y;
+        unsigned d0 = hm_prev;
+        column(Hm, E, f0, d0, qp_strip + __byte_perm(wq, 0u, 0x4440u) * qstride,
+               qp_strip + __byte_perm(wq, 0u, 0x4441u) * qstride, k, best);
+        const unsigned out_hm0 = Hm[kT - 1];
+        unsigned f1 = b.w;
+        unsigned d1 = b.x;
+        column(Hm, E, f1, d1, qp_strip + __byte_perm(wq, 0u, 0x4442u) * qstride,
+               qp_strip + __byte_perm(wq, 0u, 0x4443u) * qstride, k, best);
+        hm_prev = b.z;
+        if (!last) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
+    };
     for (int jc = 0; jc < L; jc += 8) {
         const uint4 w = w_next;
         if (jc + 8 < L) w_next = res[((jc >> 3) + 1) * kWarp + lane];
-        unsigned w0 = w.x, w1 = w.y, w2 = w.z, w3 = w.w;
 #pragma unroll 1
-        for (int h = 0; h < 4; ++h) {
-            const int j = jc + 2 * h;            // columns j and j + 1 (0-based)
-            const uint4 b = b_next;
-            if (!first && j + 2 < L) b_next = bnd[((j >> 1) + 1) * kWarp + lane];
-            // column j
-            unsigned f0 = b.y;
-            unsigned d0 = hm_prev;
-            column(Hm, E, f0, d0, qp_strip + (w0 & 0xFF) * qstride,
-                   qp_strip + ((w0 >> 8) & 0xFF) * qstride, k, best);
-            const unsigned out_hm0 = Hm[kT - 1];
-            // column j + 1
-            unsigned f1 = b.w;
-            unsigned d1 = b.x;
-            column(Hm, E, f1, d1, qp_strip + ((w0 >> 16) & 0xFF) * qstride,
-                   qp_strip + (w0 >> 24) * qstride, k, best);
-            hm_prev = b.z;
-            if (!last) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
-            w0 = w1;
-            w1 = w2;
-            w2 = w3;
+        for (int q2 = 0; q2 < 2; ++q2) {
+            two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
+            two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
         }
     }
 }
