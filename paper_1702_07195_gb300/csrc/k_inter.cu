@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const In
     }
 }
 
-// Variants: (rows per strip, warps per block).  Register budgets: 32 rows -> 121 registers
+// Variants: (rows per strip, warps per block).  Register budgets: 32 rows -> 128 registers
 // (4 blocks of 4 warps per SM); 64 rows -> <= 255 registers (2 blocks of 4 warps, or 1 of 8).
 struct InterVariant {
     int T, W;
