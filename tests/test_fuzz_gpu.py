@@ -53,20 +53,27 @@ def _case(seed):
     return A, sm, db, qs, goe, ge, cutoff, variant, split, flag_cap
 
 
-@pytest.mark.parametrize("seed", list(range(24)))
+@pytest.mark.parametrize("seed", list(range(48)))
 def test_fuzz_against_oracle(sw, seed, monkeypatch):
+    """The batch search and the single-query search of the first query; every third seed with
+    the score-profile single-query kernel."""
     A, sm, db, qs, goe, ge, cutoff, variant, split, flag_cap = _case(1000 + seed)
     if split != "-1":
         monkeypatch.setenv("SWGB_GROUP_SPLIT", split)
+    if seed % 3 == 0:
+        monkeypatch.setenv("SWGB_SCORE_PROFILE", "1")
     max_s = max(0, int(sm.max()))
     if max_s * max([len(q) for q in qs] + [1]) > 2**31 - 1:
         pytest.skip("score bound above int32")
     with sw.sw_db_load(db.residues, db.offsets, A, long_cutoff=cutoff, flag_cap=flag_cap) as h:
         sw.sw_db_set_variant(h, variant)
         got = sw.sw_search_batch(h, qs, sm, goe, ge)
+        got1 = sw.sw_search(h, qs[0], sm, goe, ge)
+    what = f"A={A}, goe={goe}, ge={ge}, cutoff={cutoff}, variant={variant}, split={split}"
     for k, q in enumerate(qs):
         exp, _ = oracle.sw_search(q, db.residues, db.offsets, sm, goe, ge)
         bad = np.nonzero(got[k].astype(np.int64) != exp)[0]
-        assert bad.size == 0, (f"seed {seed} query {k} (m={len(q)}, A={A}, goe={goe}, ge={ge}, "
-                               f"cutoff={cutoff}, variant={variant}, split={split}): "
+        assert bad.size == 0, (f"seed {seed} query {k} (m={len(q)}, {what}): "
                                f"{bad.size} mismatches, first {bad[0]}: {got[k][bad[0]]} vs {exp[bad[0]]}")
+        if k == 0:
+            np.testing.assert_array_equal(got1.astype(np.int64), exp, err_msg=f"seed {seed} alone, {what}")
