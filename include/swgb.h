@@ -102,11 +102,17 @@ typedef struct {
  * group by lane count).  Copies `residues[0 .. offsets[num_seqs])`, sequence k being
  * residues[offsets[k] .. offsets[k+1]), to the device in a length-sorted, 64-sequence
  * interleaved layout plus a plain copy.  offsets must start at 0 and be non-decreasing.
- * The caller keeps its buffers; the handle is freed with sw_db_free. */
+ * The caller keeps its buffers; the handle is freed with sw_db_free.  SW_ERR_ARG on a bad
+ * size or offset, SW_ERR_CODE on a residue code >= alphabet_size, SW_ERR_OOM when device
+ * memory runs out; *out is NULL on any error. */
 sw_status sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t num_seqs,
                      int32_t alphabet_size, sw_db **out);
+/* sw_db_load with options (Section 4 preprocessing; the placement option serves the paper's
+ * future-work case of a database larger than memory, Section 6). */
 sw_status sw_db_load_ex(const uint8_t *residues, const int64_t *offsets, int64_t num_seqs,
                         int32_t alphabet_size, const sw_db_options *opts, sw_db **out);
+/* Releases a database from sw_db_load[_ex] after its searches finish (NULL is a no-op).
+ * Sizes of the database of Section 4's preprocessing stage (-1 for a NULL handle). */
 void sw_db_free(sw_db *db);
 int64_t sw_db_num_seqs(const sw_db *db);
 int64_t sw_db_num_residues(const sw_db *db);
@@ -120,23 +126,35 @@ sw_status sw_search(const sw_db *db, const uint8_t *query, int32_t query_len,
                     const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                     int32_t *scores);
 
-/* Several queries in one persistent launch.  queries[q] has query_lens[q] residues (host).
- * scores is a host buffer of num_queries * num_seqs int32, row q = query q.  Synchronous. */
+/* SW stage (paper Section 4) for several queries in one persistent launch, work items drawn
+ * dynamically by idle blocks (the dynamic distribution of Section 4.1).  queries[q] has
+ * query_lens[q] residues (host).  scores is a host buffer of num_queries * num_seqs int32,
+ * row q = query q, original database order.  Synchronous.  Errors as sw_search. */
 sw_status sw_search_batch(const sw_db *db, const uint8_t *const *queries,
                           const int32_t *query_lens, int32_t num_queries,
                           const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                           int32_t *scores);
 
-/* Device-resident variant for callers that hold device memory (e.g. PyTorch tensors).
+/* SW stage (paper Section 4; dynamic distribution of work, Section 4.1), device-resident
+ * variant for callers that hold device memory (e.g. PyTorch tensors).
  * d_queries: device buffer of concatenated query residues; query_offsets: HOST array of
  * num_queries + 1 int64 offsets into it.  matrix: host.  d_scores: device buffer of
- * num_queries * num_seqs int32.  Work is enqueued on `stream` (a cudaStream_t, NULL = the
- * legacy default stream); the call returns without waiting for it.  Repeated calls with
- * the same shapes and pointers replay a captured CUDA graph. */
+ * num_queries * num_seqs int32 (row q = query q, original database order), owned by the
+ * caller.  Work is enqueued on `stream` (a cudaStream_t, NULL = the legacy default stream);
+ * the call returns without waiting for it.  Repeated calls with the same shapes and pointers
+ * replay a captured CUDA graph.  Argument errors are returned at once; a query residue code
+ * >= alphabet_size is detected on the device and returned as SW_ERR_CODE by the next
+ * sw_get_stats on the handle. */
 sw_status sw_search_batch_device(const sw_db *db, const uint8_t *d_queries,
                                  const int64_t *query_offsets, int32_t num_queries,
                                  const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                                  int32_t *d_scores, void *stream);
+/* The same call under the name of the asynchronous device-pointer search (Section 4 SW
+ * stage, Section 4.1 dynamic distribution): identical arguments, behaviour and errors. */
+sw_status sw_search_async(const sw_db *db, const uint8_t *d_queries,
+                          const int64_t *query_offsets, int32_t num_queries,
+                          const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                          int32_t *d_scores, void *stream);
 
 /* Autotuner.  The inter-task kernel comes in variants (query rows per strip x warps per
  * block, e.g. 32x4, 64x4, 32x8, 64x8: registers vs. occupancy vs. per-column overhead).
@@ -145,7 +163,9 @@ sw_status sw_search_batch_device(const sw_db *db, const uint8_t *d_queries,
  * variant the one every later search on `db` uses.  If `cache_path` is non-NULL the choice is
  * looked up there first (key: device name, SM count, alphabet size, database shape, probe
  * length class) and stored there after tuning; with `force` the cache is ignored on lookup.
- * The paper tunes by hand (thread counts, Section 5.2); it has no autotuner. */
+ * The counterpart of the paper's tuning of thread counts and instruction sets by measurement
+ * (Section 5.2), done here automatically per database.  Errors as sw_search; a cache file
+ * that cannot be read or written is ignored. */
 typedef struct {
     int32_t variant;             /* chosen variant index */
     int32_t rows_per_strip;      /* its query rows per strip */
@@ -159,10 +179,13 @@ sw_status sw_db_tune(sw_db *db, const uint8_t *const *queries, const int32_t *qu
                      int32_t gap_extend, const char *cache_path, int32_t force,
                      sw_tune_result *out);
 
-/* Selects an inter-task kernel variant directly (-1 restores the default). */
+/* Selects an inter-task kernel variant directly (-1 restores the default); the manual form
+ * of the Section 5.2 tuning.  SW_ERR_ARG for an unknown variant. */
 sw_status sw_db_set_variant(sw_db *db, int32_t variant);
 
-/* Measurements of the last completed search on `db` (synchronises the handle's stream). */
+/* Measurements of the last completed search on `db` (synchronises the handle's stream):
+ * kernel times and the cells of Eq. gcups (Section 5).  Returns the SW_ERR_CODE that a
+ * device-side residue check of the last search found. */
 sw_status sw_get_stats(const sw_db *db, sw_stats *out);
 
 /* ---------------------------------------------------------------- sorting stage ------- */
@@ -179,8 +202,8 @@ sw_status sw_topk(const int32_t *d_scores, int64_t num_seqs, int32_t num_queries
 
 /* ---------------------------------------------------------------- serving ------------- */
 
-/* Continuous-batching search server over a resident database (the paper searches one query
- * at a time; serving is this library's addition).  Requests (one query each) are admitted
+/* Continuous-batching search server over a resident database: not in the paper (it searches
+ * one query at a time, Section 4; serving is this library's addition).  Requests (one query each) are admitted
  * while a slot is free and their DP state fits the budget; DP state of a request = its query
  * profile ((A+1) x ceil(m/256)*256 int16) plus its score row (num_seqs int32).  The database
  * is cut into `slices` of about equal residue work; a background thread runs "ticks" that scan
@@ -216,22 +239,29 @@ typedef struct {
 
 sw_status sw_server_create(sw_db *db, const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                            const sw_server_options *opts, sw_server **out);
-/* Copies the query; returns a ticket.  SW_ERR_BUSY if max_pending requests are waiting. */
+/* Serving calls: not in the paper (a request loop on top of its Section 4 search).
+ * sw_server_submit copies the query and returns a ticket; SW_ERR_BUSY if max_pending
+ * requests are waiting, SW_ERR_ARG / SW_ERR_CODE for a bad query. */
 sw_status sw_server_submit(sw_server *srv, const uint8_t *query, int32_t query_len,
                            int64_t *ticket);
-/* If the request is done, copies its num_seqs scores to `scores`, sets *done = 1 and retires
- * the ticket; otherwise sets *done = 0. */
+/* Not in the paper (serving).  If the request is done, copies its num_seqs scores to
+ * `scores`, sets *done = 1 and retires the ticket; otherwise sets *done = 0. */
 sw_status sw_server_poll(sw_server *srv, int64_t ticket, int32_t *scores, int32_t *done);
-/* Waits up to timeout_ms (bounded; SW_ERR_TIMEOUT) for the request, then as sw_server_poll. */
+/* Not in the paper (serving).  Waits up to timeout_ms (bounded; SW_ERR_TIMEOUT) for the
+ * request, then as sw_server_poll. */
 sw_status sw_server_wait(sw_server *srv, int64_t ticket, int32_t *scores, int32_t timeout_ms);
-/* Counters and latency percentiles of completed requests (reset = 1 clears them). */
+/* Not in the paper (serving).  Counters, latency percentiles and the GCUPS of Eq. gcups
+ * over completed requests (reset = 1 clears them). */
 sw_status sw_server_get_stats(sw_server *srv, sw_server_stats *out, int32_t reset);
-/* Stops the loop (in-flight work finishes first) and frees the server. */
+/* Not in the paper (serving).  Stops the loop (in-flight work finishes first) and frees
+ * the server. */
 void sw_server_destroy(sw_server *srv);
 
 /* ---------------------------------------------------------------- host-side plan ------ */
 
-/* Host-only view of the preprocessing stage, for inspection and tests (no GPU needed).
+/* Host-only view of the preprocessing stage (paper Section 4: length sort, grouping, dummy
+ * padding), for inspection and tests (no GPU needed).  SW_ERR_ARG / SW_ERR_CODE as
+ * sw_db_load.
  * sw_layout_sizes reports the sizes; sw_layout_build fills caller-owned buffers:
  *   group_off[num_groups]   byte offset of each 64-sequence group in `inter`
  *   group_len[num_groups]   padded column count of the group (multiple of 8)
@@ -266,7 +296,8 @@ sw_status sw_layout_build(const uint8_t *residues, const int64_t *offsets, int64
  * there (with that device current); make that first call before any stream capture.
  *   d_query   device buffer of query_len residue codes (each < alphabet_size; an
  *             out-of-range code is scored as 0)
- *   matrix    host, alphabet_size x alphabet_size int8 (copied before the call returns)
+ *   matrix    host, alphabet_size x alphabet_size int8 (read before the call returns;
+ *             it reaches the device inside a kernel's parameters, not by a host copy)
  *   d_scores  device buffer of sw_db_num_seqs(db) int32, original database order
  *   stream    cudaStream_t (NULL = legacy default stream); the call only enqueues work.
  * Limits: query_len <= SW_NOALLOC_MAX_QUERY; a database whose groups or sequences are too
@@ -284,9 +315,12 @@ sw_status sw_search_noalloc(const sw_db *db, const uint8_t *d_query, int32_t que
 
 /* ---------------------------------------------------------------- misc ---------------- */
 
-const char *sw_last_error(void);      /* message for the last non-OK status (thread-local) */
+/* Library housekeeping, not in the paper: the message of the last non-OK status on this
+ * thread (never NULL), the library version, and the number of kernels this library has
+ * launched in this process. */
+const char *sw_last_error(void);
 const char *sw_version(void);
-int64_t sw_launch_count(void);        /* kernels this library has launched (process-wide) */
+int64_t sw_launch_count(void);
 
 #ifdef __cplusplus
 }

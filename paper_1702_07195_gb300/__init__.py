@@ -5,7 +5,8 @@ only, every step of the search runs in the library's CUDA kernels.  There is no 
 if the library is missing or cannot be loaded, importing this package raises.
 
 Names follow the C ABI: ``sw_db_load``, ``sw_search``, ``sw_search_batch``,
-``sw_search_batch_device``, ``sw_get_stats``, ``sw_last_error``.
+``sw_search_batch_device`` (also exported as ``sw_search_async``), ``sw_get_stats``,
+``sw_topk``, ``sw_search_noalloc``, ``Server`` (``sw_server_*``), ``sw_last_error``.
 """
 
 from __future__ import annotations
@@ -108,6 +109,8 @@ def _load():
                                            ctypes.c_int32, ctypes.c_int32, _i32p]),
         "sw_search_batch_device": (ctypes.c_int, [_vp, _vp, _i64p, ctypes.c_int32, _i8p,
                                                   ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+        "sw_search_async": (ctypes.c_int, [_vp, _vp, _i64p, ctypes.c_int32, _i8p,
+                                           ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
         "sw_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
         "sw_search_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _i8p, ctypes.c_int32,
                                              ctypes.c_int32, _vp, _vp]),
@@ -302,6 +305,10 @@ def sw_search_batch_device(db: Database, d_queries, query_offsets, matrix, gap_o
     _check(lib.sw_search_batch_device(db.handle, _vp(d_queries.data_ptr()), _ptr(o, _i64p), nq,
                                       _ptr(m, _i8p), int(gap_open), int(gap_extend),
                                       _vp(d_scores.data_ptr()), _vp(s)))
+
+
+# The boundary's name for the asynchronous device-pointer search; same call.
+sw_search_async = sw_search_batch_device
 
 
 def sw_search_noalloc(db: Database, d_query, matrix, gap_open: int, gap_extend: int, d_scores,

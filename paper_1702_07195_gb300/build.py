@@ -16,8 +16,6 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libswgb.so")
-PROBE_SRC = os.path.join(PKG, "probe", "simd_rates.cu")
-PROBE = os.path.join(OUT_DIR, "simd_rates")   # packed-integer operation rates (int8 tier study)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,10 +36,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(PROBE):
+    if not os.path.exists(LIB):
         return False
-    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE))
-    return all(os.path.getmtime(p) <= t for p in _deps() + [PROBE_SRC])
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(p) <= t for p in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
@@ -64,16 +62,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    def compile_probe():
-        r = subprocess.run([nvcc] + ARCH + ["-O3", "-std=c++17", PROBE_SRC, "-o", PROBE],
-                           capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
-
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        probe = ex.submit(compile_probe)
         results = list(ex.map(compile_one, sources()))
-        probe.result()
     if verbose:
         for _, err in results:
             if err.strip():

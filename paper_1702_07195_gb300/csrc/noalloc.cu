@@ -18,8 +18,9 @@
 // point runs, held until the process exits.  (With CUDA's default lazy module loading the
 // array is reserved when the first call on a device resolves its address.)  Because the
 // boundary buffers are bounded, the inter-task kernel runs on as many blocks as fit in them
-// (about 64 blocks for databases whose longest group has 2,000 columns), so this path is
-// slower than sw_search_batch_device on large databases.
+// (a warp's buffer takes 16 bytes per column pair and thread: 512 KB for a longest group of
+// 2,000 columns, 2 MB for a 4-warp block, so about 32 blocks fit in kBndBytes), so this path
+// is slower than sw_search_batch_device on large databases.
 //
 // The same kernels as the regular search run here (query profile, int16x2 inter-task
 // kernel, int32 intra-task kernel for long subjects and for saturated lanes); only the
@@ -90,6 +91,34 @@ sw_status scratch_base(int dev, unsigned char** out) {
     }
     *out = g_base[dev];
     return SW_OK;
+}
+
+// Per-call tables, passed by value as kernel parameters (about 1.1 KB) and written into the
+// array by k_noalloc_setup: no host staging buffer and no host-to-device copy.
+struct NoallocSetup {
+    QueryDesc desc;
+    int64_t query_len;
+    int32_t m_pad;
+    int32_t matrix_bytes;
+    int8_t matrix[kMaxAlphabet * kMaxAlphabet];
+};
+
+// Writes the one-query tables (descriptor, profile offset and padded length, query offsets,
+// query order, matrix) and zeroes the control block: the array keeps the previous call's
+// contents, and the counters must start at zero.
+__global__ void k_noalloc_setup(const NoallocSetup s, Control* ctrl, QueryDesc* desc,
+                                int64_t* qp_off, int32_t* mpad, int64_t* qoff, int32_t* order,
+                                int8_t* dmat) {
+    for (int i = threadIdx.x; i < s.matrix_bytes; i += blockDim.x) dmat[i] = s.matrix[i];
+    if (threadIdx.x == 0) {
+        *ctrl = Control{};
+        *desc = s.desc;
+        *qp_off = 0;
+        *mpad = s.m_pad;
+        qoff[0] = 0;
+        qoff[1] = s.query_len;
+        *order = 0;
+    }
 }
 
 // Work list for one query: chunks of `w` groups, longest groups first.
@@ -199,22 +228,17 @@ extern "C" sw_status sw_search_noalloc(const sw_db* db, const uint8_t* d_query, 
     const int32_t m_pad = static_cast<int32_t>((query_len + kQpRows - 1) / kQpRows * kQpRows);
     const uint32_t flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::min<int64_t>(N, kMaxFlags), v.flag_cap));
 
-    // Small per-call tables: copied from the stack (the copy has read them when it returns).
-    const QueryDesc h_desc{qp, d_scores, query_len, m_pad};
-    const int64_t h_qp_off = 0;
-    const int32_t h_mpad = m_pad;
-    const int64_t h_qoff[2] = {0, query_len};
-    const int32_t h_order = 0;
-    NA_CU(cudaMemcpyAsync(desc, &h_desc, sizeof(h_desc), cudaMemcpyHostToDevice, st));
-    NA_CU(cudaMemcpyAsync(qp_off, &h_qp_off, sizeof(h_qp_off), cudaMemcpyHostToDevice, st));
-    NA_CU(cudaMemcpyAsync(mpad, &h_mpad, sizeof(h_mpad), cudaMemcpyHostToDevice, st));
-    NA_CU(cudaMemcpyAsync(qoff, h_qoff, sizeof(h_qoff), cudaMemcpyHostToDevice, st));
-    NA_CU(cudaMemcpyAsync(order, &h_order, sizeof(h_order), cudaMemcpyHostToDevice, st));
-    NA_CU(cudaMemcpyAsync(dmat, matrix, static_cast<size_t>(A * A), cudaMemcpyHostToDevice, st));
-    // The array keeps the previous call's contents: the counters must start at zero.
-    NA_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), st));
+    // Small per-call tables travel as kernel parameters (captured by value at launch).
+    NoallocSetup setup{};
+    setup.desc = QueryDesc{qp, d_scores, query_len, m_pad};
+    setup.query_len = query_len;
+    setup.m_pad = m_pad;
+    setup.matrix_bytes = A * A;
+    for (int i = 0; i < A * A; ++i) setup.matrix[i] = matrix[i];
+    k_noalloc_setup<<<1, 256, 0, st>>>(setup, ctrl, desc, qp_off, mpad, qoff, order, dmat);
+    NA_CU(cudaGetLastError());
 
-    int64_t launches = 0;
+    int64_t launches = 1;
     NA_CU(launch_build_qp(d_query, qoff, 1, dmat, A, qp_bias, qp_off, mpad, qp, m_pad, ctrl, st));
     ++launches;
     const Gaps gaps{goe, ge, gep};

@@ -877,6 +877,13 @@ sw_status sw_search_batch_device(const sw_db* cdb, const uint8_t* d_queries,
                          d_scores, static_cast<cudaStream_t>(stream));
 }
 
+sw_status sw_search_async(const sw_db* db, const uint8_t* d_queries, const int64_t* query_offsets,
+                          int32_t num_queries, const int8_t* matrix, int32_t gap_open,
+                          int32_t gap_extend, int32_t* d_scores, void* stream) {
+    return sw_search_batch_device(db, d_queries, query_offsets, num_queries, matrix, gap_open,
+                                  gap_extend, d_scores, stream);
+}
+
 sw_status sw_search_batch(const sw_db* cdb, const uint8_t* const* queries,
                           const int32_t* query_lens, int32_t num_queries, const int8_t* matrix,
                           int32_t gap_open, int32_t gap_extend, int32_t* scores) {

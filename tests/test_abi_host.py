@@ -44,6 +44,33 @@ def test_exports_every_declared_symbol(sw):
     assert sw.lib.sw_version().decode().startswith("swgb")
 
 
+def _declaration_docs():
+    """(function name, the last column-0 comment before its declaration) for include/*.h."""
+    out = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        comments = [(m.start(), m.group(0)) for m in re.finditer(r"^/\*.*?\*/", text, flags=re.S | re.M)
+                    if not m.group(0).startswith("/* ----")]
+        bare = re.sub(r"/\*.*?\*/", lambda m: " " * len(m.group(0)), text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*"
+                             r"([a-z][A-Za-z0-9_]*)\s*\(", bare, flags=re.M):
+            doc = [c for pos, c in comments if pos < m.start(1)]
+            out.append((m.group(1), doc[-1] if doc else ""))
+    return out
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment names the paper passage that defines it (a section or an
+    equation) or says that the paper has none (serving, housekeeping, no-allocation search)."""
+    docs = _declaration_docs()
+    assert len(docs) >= 25
+    cite = re.compile(r"Section \d|Eq\. |Eqs\. |[Nn]ot in the paper|no counterpart")
+    missing = [name for name, doc in docs if not cite.search(doc)]
+    assert not missing, f"declarations without a citation: {missing}"
+    names = {n for n, _ in docs}
+    assert {"sw_search_async", "sw_search_batch_device", "sw_db_tune", "sw_server_create"} <= names
+
+
 def _reconstruct(lay, num_seqs):
     goff, glen, perm, inter = lay["group_off"], lay["group_len"], lay["perm"], lay["inter"]
     seqs = {}

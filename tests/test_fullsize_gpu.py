@@ -1,8 +1,14 @@
 """Parity at full workload sizes, in the launch configuration bench.py times
-(sw_search_batch_device on device buffers, autotuned kernel variant): every score is checked
-by properties that hold at any size, and a seeded sample of (query, sequence) pairs -- the
-longest sequences and the highest scores included -- is recomputed one by one by the oracle
-and must match bit for bit."""
+(sw_search_batch_device on device buffers, autotuned kernel variant).  Every score is checked
+by properties that hold at any size; the headline workload's 20 x 1M scores are all compared
+with the oracle's (stored per-row hashes written by tests/golden/make_fullsize_golden.py from
+the oracle alone); the paper-shaped and long-subject workloads, too large for a full oracle
+pass, are compared with stored oracle scores of their longest subjects against every query
+and of seeded random pairs.  Tolerance 0 (integer scores)."""
+
+import hashlib
+import json
+import os
 
 import numpy as np
 import pytest
@@ -73,29 +79,97 @@ def _check_properties(wl, got):
         assert (got[q][lens == 0] == 0).all()
 
 
+def _golden(name, wl):
+    """Stored oracle results of a full-size workload (written by tests/golden/
+    make_fullsize_golden.py from the oracle alone), after checking they were made from these
+    very inputs."""
+    path = os.path.join(os.path.dirname(__file__), "golden", f"fullsize_{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        doc = json.load(f)
+    fp = doc["inputs"]
+    assert fp["num_seqs"] == wl.db.num_seqs and fp["num_residues"] == wl.db.num_residues
+    assert fp["queries"] == [_sha(q) for q in wl.queries], "query generator changed"
+    assert fp["residues"] == _sha(wl.db.residues), "database generator changed"
+    assert fp["offsets"] == _sha(wl.db.offsets.astype("<i8"))
+    assert fp["matrix"] == _sha(wl.matrix.astype(np.int8))
+    return doc
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _check_rows(wl, got, doc):
+    """Every score: each int32 row's SHA-256 against the oracle's.  A row that differs is
+    narrowed to its blocks by the stored block hashes, and the first differing block is
+    recomputed by the oracle to name the first wrong score."""
+    blk = doc["block"]
+    for q, rec in enumerate(doc["rows"]):
+        row = np.ascontiguousarray(got[q], dtype="<i4")
+        assert int(row.max()) == rec["max"] and int(np.argmax(row)) == rec["argmax"], \
+            f"query {q}: max/argmax {int(row.max())}/{int(np.argmax(row))} vs oracle {rec['max']}/{rec['argmax']}"
+        if _sha(row) == rec["sha256"]:
+            continue
+        bad = [b for b, h in zip(range(0, row.size, blk), rec["blocks"]) if _sha(row[b:b + blk])[:16] != h]
+        b0 = bad[0]
+        idx = np.arange(b0, min(row.size, b0 + blk), dtype=np.int64)
+        exp = oracle.sw_pairs(wl.queries, wl.db.residues, wl.db.offsets,
+                              np.full(idx.size, q, np.int64), idx, wl.matrix, 10, 2)
+        wrong = np.nonzero(row[idx].astype(np.int64) != exp)[0]
+        first = int(idx[wrong[0]]) if wrong.size else -1
+        raise AssertionError(f"query {q} (m={len(wl.queries[q])}): {len(bad)} blocks of {blk} "
+                             f"differ; first wrong score at sequence {first}: "
+                             f"gpu {row[first] if first >= 0 else None} oracle "
+                             f"{exp[wrong[0]] if wrong.size else None}")
+
+
+def _check_pairs(got, doc):
+    bad = [(q, d, int(got[q, d]), e) for q, d, e in doc["pairs"] if int(got[q, d]) != e]
+    assert not bad, f"{len(bad)} of {len(doc['pairs'])} stored oracle scores differ: {bad[:5]}"
+    return len(doc["pairs"])
+
+
 def test_batched_full_size(sw):
-    """20 queries (144..5478) vs 1M sequences: the default benchmark workload."""
+    """20 queries (144..5478) vs 1M sequences, the headline workload: all 20,000,000 scores
+    against the stored oracle rows."""
     wl = w.batched()
     got, st = _run_like_bench(sw, wl)
     assert st["multi_query"] == 1 and st["graph_replay"] == 1
     _check_properties(wl, got)
-    assert _check_sample(wl, got, 300, seed=1) >= 300
+    doc = _golden("batched", wl)
+    if doc is None:
+        assert _check_sample(wl, got, 300, seed=1) >= 300
+        pytest.skip("tests/golden/fullsize_batched.json absent: checked a sample only")
+    _check_rows(wl, got, doc)
 
 
 def test_paper_shaped_full_size(sw):
-    """20 queries vs 6M sequences (1.5G residues, lengths up to 35,000): inter-task kernel for
-    the bulk, intra-task kernel for the subjects above the cutoff."""
-    wl = w.paper_shaped(query_lengths=[144, 807, 5478])
+    """The 20 queries vs 6M sequences (1.5G residues, lengths up to 35,000): inter-task kernel
+    for the bulk, intra-task kernel for the subjects above the cutoff; stored oracle scores of
+    the 20 longest subjects against every query and of random pairs, and a fresh sample."""
+    wl = w.paper_shaped()
     got, st = _run_like_bench(sw, wl)
     assert st["intra_ms"] > 0
     _check_properties(wl, got)
-    _check_sample(wl, got, 200, seed=2)
+    _check_sample(wl, got, 50, seed=2)
+    doc = _golden("paper_shaped", wl)
+    if doc is None:
+        pytest.skip("tests/golden/fullsize_paper_shaped.json absent: checked a sample only")
+    assert _check_pairs(got, doc) >= 1000
 
 
 def test_long_subject_full_size(sw):
-    """5 queries (1,000..5,000) vs 50,000 subjects of 5,000..35,000 residues: all intra-task."""
+    """5 queries (1,000..5,000) vs 50,000 subjects of 5,000..35,000 residues, all intra-task:
+    stored oracle scores of the 50 longest subjects against every query and of random pairs
+    (2,000 pairs)."""
     wl = w.long_subject()
     got, st = _run_like_bench(sw, wl, tune=False)
     assert st["inter_cells"] == 0 and st["intra_ms"] > 0
     _check_properties(wl, got)
-    _check_sample(wl, got, 25, seed=3)
+    doc = _golden("long_subject", wl)
+    if doc is None:
+        _check_sample(wl, got, 25, seed=3)
+        pytest.skip("tests/golden/fullsize_long_subject.json absent: checked a sample only")
+    assert _check_pairs(got, doc) >= 2000

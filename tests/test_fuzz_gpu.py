@@ -55,8 +55,9 @@ def _case(seed):
 
 @pytest.mark.parametrize("seed", list(range(48)))
 def test_fuzz_against_oracle(sw, seed, monkeypatch):
-    """The batch search and the single-query search of the first query; every third seed with
-    the score-profile single-query kernel."""
+    """The batch search, the single-query search of the first query and the no-allocation
+    search of the first query; every third seed with the score-profile single-query kernel."""
+    import torch
     A, sm, db, qs, goe, ge, cutoff, variant, split, flag_cap = _case(1000 + seed)
     if split != "-1":
         monkeypatch.setenv("SWGB_GROUP_SPLIT", split)
@@ -69,6 +70,12 @@ def test_fuzz_against_oracle(sw, seed, monkeypatch):
         sw.sw_db_set_variant(h, variant)
         got = sw.sw_search_batch(h, qs, sm, goe, ge)
         got1 = sw.sw_search(h, qs[0], sm, goe, ge)
+        got_na = None
+        if len(qs[0]) <= 8192:                   # SW_NOALLOC_MAX_QUERY
+            d_q = torch.from_numpy(qs[0]).cuda()
+            d_s = torch.full((h.num_seqs,), -9, dtype=torch.int32, device="cuda")
+            sw.sw_search_noalloc(h, d_q, sm, goe, ge, d_s)
+            got_na = d_s.cpu().numpy()
     what = f"A={A}, goe={goe}, ge={ge}, cutoff={cutoff}, variant={variant}, split={split}"
     for k, q in enumerate(qs):
         exp, _ = oracle.sw_search(q, db.residues, db.offsets, sm, goe, ge)
@@ -77,3 +84,6 @@ def test_fuzz_against_oracle(sw, seed, monkeypatch):
                                f"{bad.size} mismatches, first {bad[0]}: {got[k][bad[0]]} vs {exp[bad[0]]}")
         if k == 0:
             np.testing.assert_array_equal(got1.astype(np.int64), exp, err_msg=f"seed {seed} alone, {what}")
+            if got_na is not None:
+                np.testing.assert_array_equal(got_na.astype(np.int64), exp,
+                                              err_msg=f"seed {seed} no-allocation search, {what}")

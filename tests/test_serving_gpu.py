@@ -44,7 +44,7 @@ def test_alone_equals_mix_equals_oracle(sw):
             st = srv.stats()
     for k, (a, b) in enumerate(zip(alone, mix)):
         assert np.array_equal(a, b), f"request {k}: alone != mix"
-    for k in (0, 3, len(qs) - 2, len(qs) - 1):
+    for k in range(len(qs)):                                         # every request
         exp, _ = oracle.sw_search(qs[k], db.residues, db.offsets, sm, 10, 2)
         assert np.array_equal(mix[k].astype(np.int64), exp), f"request {k} vs oracle"
     assert int(mix[len(qs) - 2].max()) > 32767
@@ -74,6 +74,8 @@ def test_arrivals_join_running_ticks(sw):
             st = srv.stats(reset=True)
     for k in range(len(qs)):
         assert np.array_equal(out[k], ref[k]), f"request {k}"
+        exp, _ = oracle.sw_search(qs[k], wl.db.residues, wl.db.offsets, wl.matrix, 10, 2)
+        assert np.array_equal(out[k].astype(np.int64), exp), f"request {k} vs oracle"
     assert st["joined_while_running"] >= 1 and st["ticks"] >= 2
     assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
 
@@ -137,6 +139,8 @@ def test_concurrent_clients(sw):
     assert not errors, errors
     for k in range(len(qs)):
         assert np.array_equal(out[k], ref[k]), f"request {k}"
+        exp, _ = oracle.sw_search(qs[k], wl.db.residues, wl.db.offsets, wl.matrix, 10, 2)
+        assert np.array_equal(out[k].astype(np.int64), exp), f"request {k} vs oracle"
     assert st["completed"] == len(qs)
 
 
