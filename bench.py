@@ -351,7 +351,17 @@ def roofline_of(sw, st, workload, sms, f_max, peaks, peak_src, clocks):
     library's per-launch CUDA events of the last timed step."""
     inter_cells = st["inter_cells"]
     intra_cells = st["cells"] - inter_cells
-    if st["intra_ms"] > st["inter_ms"]:
+    if st["intra_ms"] > st["inter_ms"] and st.get("intra_packed"):
+        # packed int16x2 wavefront kernel: two queries per register (batches) or two subjects
+        # per register (one query); the same 5.5-operation basis as the inter-task kernels
+        kernel = "k_wave_mq_i16x2" if st["intra_packed"] == 1 else "k_wave_ss_i16x2"
+        k_ms, k_cells = st["intra_ms"], intra_cells
+        peak = sms * LANE_OPS_PER_CLK_SM * f_max * 2.0 / OPS_PER_CELL_PAIR / 1e9
+        basis = (f"{sms} SMs x {LANE_OPS_PER_CLK_SM} ALU-pipe int16x2 lane-ops/clk x "
+                 f"{f_max / 1e6:.0f} MHz x 2 cells / {OPS_PER_CELL_PAIR} DPX ops per "
+                 "cell pair (ALU-pipe bound; HBM is not the bound)")
+        rows = None
+    elif st["intra_ms"] > st["inter_ms"]:
         kernel, k_ms, k_cells = "k_intra_block_i32", st["intra_ms"], intra_cells
         peak = sms * LANE_OPS_PER_CLK_SM * f_max / ALU_OPS_PER_CELL_I32 / 1e9
         basis = (f"{sms} SMs x {LANE_OPS_PER_CLK_SM} ALU-pipe int32 lane-ops/clk x "

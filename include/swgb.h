@@ -34,7 +34,8 @@
  * load), SWGB_GROUP_SPLIT=s (groups [0, s) on the inter-task kernel, the rest on the int32
  * intra-task kernel), SWGB_INTRA_BLOCK=0 (per-warp int32 kernel, read at load),
  * SWGB_INTRA_BLOCKS_PER_SM=n, SWGB_SCORE_PROFILE=1 (score-profile single-query kernel,
- * Section 4.3), SWGB_GRAPHS=0 (no CUDA-graph capture).  Scores do not depend on them.
+ * Section 4.3), SWGB_WAVE=0 (int32 instead of the packed int16x2 wavefront kernel for long
+ * subjects), SWGB_GRAPHS=0 (no CUDA-graph capture).  Scores do not depend on them.
  */
 #ifndef SWGB_H
 #define SWGB_H
@@ -94,6 +95,11 @@ typedef struct {
     int32_t multi_query;   /* 1 if two queries shared each register (two or more queries) */
     int32_t score_profile; /* 1 if the single-query inter-task kernel used a score profile
                               (Section 4.3; environment SWGB_SCORE_PROFILE=1) */
+    int32_t intra_packed;  /* intra-task work on the packed int16x2 wavefront kernel instead
+                              of int32: 1 = two queries per register (long subjects of a
+                              batch), 2 = two subjects per register (routed groups of a
+                              one-query search), 0 = int32 only */
+    int32_t reserved;
 } sw_stats;
 
 /* ---------------------------------------------------------------- database ------------ */

@@ -21,6 +21,7 @@
 // permutation of the banks, so those loads are conflict-free as they are.
 #include <type_traits>
 
+#include "slice_layout.cuh"
 #include "swgb_device.cuh"
 
 namespace swgb {
@@ -66,57 +67,6 @@ __device__ bool decode_item(const IntraParams& p, unsigned long long it, BlockIt
     }
     return true;
 }
-
-// Word offset of lane `lane`'s chunk of kTB rows inside one residue's slice row.  Chunks are
-// w = kTB / 4 bank groups (16 bytes each) wide and packed in w segments of 32 / w chunks, each
-// segment one group further along than a packed layout would put it; the lane -> (segment,
-// chunk) map gives the 8 lanes of a quarter-warp 8 distinct starting groups modulo 8.
-template <int kTB>
-__host__ __device__ constexpr int chunk_offset(int lane) {
-    if (kTB % 2 == 1) return kTB * lane;
-    constexpr int w = kTB / 4;
-    constexpr int per_q = 8 / w;                   // lanes of a quarter-warp per segment
-    const int q = lane >> 3, i = lane & 7;
-    const int seg = i / per_q, c = q * per_q + i % per_q;
-    return 4 * (33 * seg + w * c);
-}
-
-// Words per residue row of the slice: the span of the chunks rounded up to 32 words.
-template <int kTB>
-__host__ __device__ constexpr int slice_stride() {
-    return kTB % 2 == 1 ? (kTB * kWarp + 31) / 32 * 32 : (4 * (33 * (kTB / 4) - 1) + 31) / 32 * 32;
-}
-
-template <int kTB>
-constexpr bool chunks_conflict_free() {
-    bool ok = slice_stride<kTB>() % 32 == 0;   // the residue does not move the bank
-    if (kTB % 2 == 1) {
-        for (int k = 0; k < kTB; ++k) {        // 4-byte loads: one bank per lane
-            unsigned long long seen = 0;
-            for (int l = 0; l < kWarp; ++l) seen |= 1ull << ((chunk_offset<kTB>(l) + k) % 32);
-            ok = ok && seen == 0xFFFFFFFFull;
-        }
-    } else {
-        for (int q = 0; q < 4; ++q) {          // 16-byte loads: 8 groups per quarter-warp
-            unsigned seen = 0;
-            for (int i = 0; i < 8; ++i) {
-                const int off = chunk_offset<kTB>(8 * q + i);
-                ok = ok && off % 4 == 0;
-                seen |= 1u << ((off / 4) % 8);
-            }
-            ok = ok && seen == 0xFFu;
-        }
-    }
-    for (int l = 0; l < kWarp; ++l)            // chunks lie inside the row, disjoint
-        for (int m = 0; m < kWarp; ++m) {
-            const int a = chunk_offset<kTB>(l), b = chunk_offset<kTB>(m);
-            ok = ok && a + kTB <= slice_stride<kTB>();
-            ok = ok && (l == m || a >= b + kTB || b >= a + kTB);
-        }
-    return ok;
-}
-static_assert(chunks_conflict_free<5>() && chunks_conflict_free<8>() && chunks_conflict_free<16>(),
-              "profile slice layout");
 
 // One query row of the column step: the cell update of Eqs. sw2-sw4 on (H - Goe) state.
 __device__ __forceinline__ int cell_i32(int& d, int& hm, int& e, int& f, int sc, int goe, int ge,

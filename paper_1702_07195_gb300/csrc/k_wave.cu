@@ -1,0 +1,464 @@
+// Intra-task Smith-Waterman/Gotoh wavefront on packed int16x2 lanes.
+//
+// The int32 intra-task kernels (k_intra_i32, k_intra_block_i32) give one warp one (query,
+// subject) pair: lane l owns kTB query rows of a pass and updates column t - l at step t, the
+// bottom row of each lane reaching the next lane by __shfl_up_sync (the intra-task scheme of
+// Section 1, on Eqs. sw2-sw4 of Section 2).  This kernel runs the same wavefront with the
+// DPX int16x2 operations of the inter-task kernels, two alignments per register, and therefore
+// two cells per lane-operation:
+//
+//  two-query mode (k_wave_mq_i16x2): a warp aligns ONE subject against two streams of query
+//  passes, pass k of stream a in the low halves and pass k of stream b in the high halves of
+//  its registers (the pairing of the multi-query inter-task kernel, MqStep lists with
+//  32 x kTB rows per step).  Both halves read the same subject residue, so one 16-byte load of
+//  the paired profile pp[d][row] = (S'_a, S'_b) gives four packed score pairs: 5.5 DPX
+//  operations per cell pair, the inter-task kernels' minimum.  At the first pass of a query
+//  in one half, that half starts from the zero boundary (its lane-0 input is masked to the
+//  initial values); at its last pass the half's running best is reduced over the warp and
+//  emitted.
+//
+//  two-subject mode (k_wave_ss_i16x2): a search with one query; a warp aligns the query
+//  against the two subjects in slots 2t and 2t + 1 of an interleaved 64-sequence group, one in
+//  each half.  The group layout puts the two subjects' residues of a column in adjacent bytes
+//  (one 16-bit load per step), and the two score rows come from the query profile: the slice
+//  of a pass holds, per residue and lane, the lane's rows as int16 pairs (rows 2w, 2w + 1 in
+//  word w), and a byte permute of the two residues' words gives each row's packed pair
+//  (6.5 operations per cell pair instead of 5.5).  Beyond a subject's end its half reads the
+//  dummy code, whose score 0 leaves its best unchanged.  This mode serves the groups that a
+//  small database routes off the inter-task kernel (one warp per 64 subjects cannot fill the
+//  GPU there).
+//
+// Saturation (Section 4.2): every intermediate lies in [-2 Goe - Ge, best + max SM] until the
+// running best of a half reaches 32767 - max SM, so an alignment whose best stays below that
+// threshold is exact; one that reaches it is written as -1 and listed for the int32 rescore,
+// like the inter-task kernels' lanes.  The pass-boundary row (H - Goe, F) of each column goes
+// through a per-warp global buffer as one int2 of packed pairs, written by lane 31 and read by
+// lane 0 of the next pass, 32 columns at a time.
+#include <type_traits>
+
+#include "slice_layout.cuh"
+#include "swgb_device.cuh"
+
+namespace swgb {
+
+namespace {
+
+constexpr int kWaveBW = 8;   // warps per block: the subjects that share one profile slice
+
+struct PackedGaps {
+    unsigned ngoe, nge, ngep, floor;
+};
+
+__device__ __forceinline__ unsigned pack2(int v) {
+    return (static_cast<unsigned>(v) & 0xFFFFu) * 0x00010001u;
+}
+
+// One query row of a column step on both halves: Eqs. sw2-sw4 on (H - Goe) state with the
+// biased score S' = SM + Goe (the same update as the inter-task kernels).
+__device__ __forceinline__ unsigned cell2(unsigned& d, unsigned& hm, unsigned& e, unsigned& f,
+                                          unsigned sc, const PackedGaps& k) {
+    const unsigned x = __viaddmax_s16x2_relu(d, sc, e);      // max(0, H_diag + S, E)
+    const unsigned xm = __viaddmax_s16x2(x, k.ngoe, k.floor);  // X - Goe
+    d = hm;
+    hm = __viaddmax_s16x2(f, k.ngoe, xm);                    // H - Goe = max(F, X) - Goe
+    e = __viaddmax_s16x2(e, k.nge, hm);                      // E of the next column
+    f = __viaddmax_s16x2(f, k.ngep, xm);                     // F of the next row
+    return x;
+}
+
+__device__ __forceinline__ void emit_score(const WaveParams& p, int q, int id, int v) {
+    if (id < 0 || q < 0) return;
+    int32_t* scores = p.queries[q].scores;
+    if (v >= p.thresh) {
+        scores[id] = -1;
+        const unsigned slot = atomicAdd(&p.ctrl->flag_count, 1u);
+        if (slot < p.flag_cap) p.flags[slot] = FlagEntry{q, id};
+    } else {
+        scores[id] = v;
+    }
+}
+
+__device__ __forceinline__ uint2 mask_boundary(uint2 v, unsigned keep, unsigned init_hm,
+                                               unsigned init_f) {
+    v.x = (v.x & keep) | (init_hm & ~keep);
+    v.y = (v.y & keep) | (init_f & ~keep);
+    return v;
+}
+
+// kTB query rows per lane (passes of 32 * kTB rows), kWaveBW warps per block: block item i
+// takes subjects [i * kWaveBW, (i + 1) * kWaveBW) of the list (longest first), one per warp,
+// and runs every step of the two-stream pass list over them.
+template <int kTB>
+__global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WaveParams p) {
+    constexpr int kBlock = kWaveBW * kWarp;
+    constexpr int kRowsB = kTB * kWarp;
+    constexpr int kPStride = slice_stride<kTB>();   // words per residue row of the slice
+    static_assert(kTB % 4 == 0, "rows per lane: whole 16-byte profile loads");
+    extern __shared__ __align__(16) uint32_t s_pp[];   // (A + 1) x kPStride
+    __shared__ int s_item;
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warp = threadIdx.x >> 5;
+    const int my_chunk = chunk_offset<kTB>(lane);
+    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kWaveBW + warp) * p.spill_stride;
+    PackedGaps k;
+    k.ngoe = pack2(-p.gaps.goe);
+    k.nge = pack2(-p.gaps.ge);
+    k.ngep = pack2(-p.gaps.gep);
+    k.floor = 0x80008000u;
+    const unsigned init_hm = k.ngoe, init_f = k.ngep;   // (H - Goe, F) of the zero boundary
+
+    for (;;) {
+        __syncthreads();   // s_item of the previous item has been read by every warp
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_wave, 1u));
+        __syncthreads();
+        const int64_t first_subject = static_cast<int64_t>(s_item) * kWaveBW;
+        if (first_subject >= p.num_subjects) break;
+        const int64_t si = first_subject + warp;
+        const int seq = si < p.num_subjects ? p.subjects[si] : -1;
+        int n = 0;
+        const uint8_t* subj = nullptr;
+        if (seq >= 0) {
+            const int64_t off = p.plain_off[seq];
+            n = static_cast<int>(p.plain_off[seq + 1] - off);
+            subj = p.plain + off;
+        }
+        unsigned best = 0;
+        for (int ks = 0; ks < p.num_steps; ++ks) {
+            __syncthreads();   // everyone is done with the previous slice
+            const int64_t row0 = static_cast<int64_t>(ks) * kRowsB;
+            for (int v = threadIdx.x; v < p.alphabet1 * kRowsB; v += kBlock) {
+                const int d = v / kRowsB;
+                const int r = v - d * kRowsB;
+                s_pp[d * kPStride + chunk_offset<kTB>(r / kTB) + r % kTB] =
+                    p.pp[static_cast<int64_t>(d) * p.rows_pad + row0 + r];
+            }
+            __syncthreads();
+            const MqStep st = p.steps[ks];
+            // halves that start a query here begin at the zero boundary
+            const unsigned keep = ((st.flags & kMqFirstA) ? 0u : 0x0000FFFFu) |
+                                  ((st.flags & kMqFirstB) ? 0u : 0xFFFF0000u);
+            const bool write = ks + 1 < p.num_steps;
+            if (n > 0) {
+                unsigned Hm[kTB], E[kTB];
+#pragma unroll
+                for (int r = 0; r < kTB; ++r) {
+                    Hm[r] = init_hm;
+                    E[r] = init_f;
+                }
+                unsigned hm_prev = init_hm;
+                unsigned out_hm = init_hm, out_f = init_f;
+                uint2 sp_cur = make_uint2(init_hm, init_f), sp_next = sp_cur;
+                if (keep != 0u) {
+                    if (lane < n)
+                        sp_cur = mask_boundary(reinterpret_cast<const uint2*>(spill)[lane], keep,
+                                               init_hm, init_f);
+                    if (32 + lane < n)
+                        sp_next = mask_boundary(reinterpret_cast<const uint2*>(spill)[32 + lane],
+                                                keep, init_hm, init_f);
+                }
+                unsigned res_next = lane == 0 ? subj[0] : 0u;
+                const int steps = n + kWarp - 1;
+                // Step t: lane l updates column j = t - l.  Lane 0 takes the previous pass's row
+                // of column t from lane (t mod 32) of sp_cur (columns [32 k, 32 k + 32) during
+                // steps [32 k, 32 k + 32)); when both halves start a query (`on_first`) that row
+                // is the zero boundary, a constant.  The residue of the next step's column is
+                // loaded one step ahead.
+                auto step = [&](const int t, const int src, auto checked, auto on_first) {
+                    const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
+                    const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
+                    unsigned l0_hm = init_hm, l0_f = init_f;
+                    if constexpr (!decltype(on_first)::value) {
+                        l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
+                        l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                    }
+                    const int j = t - lane;
+                    const unsigned res = res_next;
+                    if (j + 1 >= 0 && j + 1 < n) res_next = subj[j + 1];
+                    if (decltype(checked)::value && !(j >= 0 && j < n)) return;
+                    unsigned F = lane == 0 ? l0_f : up_f;     // F(r0, j)
+                    unsigned d = hm_prev;                      // (H - Goe)(r0 - 1, j - 1)
+                    hm_prev = lane == 0 ? l0_hm : up_hm;       // (H - Goe)(r0 - 1, j)
+                    const uint4* prow = reinterpret_cast<const uint4*>(s_pp + res * kPStride + my_chunk);
+#pragma unroll
+                    for (int r4 = 0; r4 < kTB; r4 += 4) {
+                        const uint4 sv = prow[r4 >> 2];
+                        const unsigned x0 = cell2(d, Hm[r4], E[r4], F, sv.x, k);
+                        const unsigned x1 = cell2(d, Hm[r4 + 1], E[r4 + 1], F, sv.y, k);
+                        best = __vimax3_s16x2(best, x0, x1);
+                        const unsigned x2 = cell2(d, Hm[r4 + 2], E[r4 + 2], F, sv.z, k);
+                        const unsigned x3 = cell2(d, Hm[r4 + 3], E[r4 + 3], F, sv.w, k);
+                        best = __vimax3_s16x2(best, x2, x3);
+                    }
+                    out_hm = Hm[kTB - 1];
+                    out_f = F;
+                    if (lane == kWarp - 1 && write) spill[j] = make_int2(static_cast<int>(out_hm),
+                                                                         static_cast<int>(out_f));
+                };
+                auto run = [&](auto on_first) {
+                    for (int tb = 0; tb < steps; tb += kWarp) {
+                        if constexpr (!decltype(on_first)::value) {
+                            if (tb > 0) {
+                                sp_cur = sp_next;
+                                if (tb + 32 + lane < n)
+                                    sp_next = mask_boundary(
+                                        reinterpret_cast<const uint2*>(spill)[tb + 32 + lane],
+                                        keep, init_hm, init_f);
+                            }
+                        }
+                        if (tb >= kWarp && tb + kWarp <= n) {
+#pragma unroll 1
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        } else {
+                            const int ue = min(kWarp, steps - tb);
+#pragma unroll 1
+                            for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{}, on_first);
+                        }
+                    }
+                };
+                if (keep == 0u)
+                    run(std::true_type{});
+                else
+                    run(std::false_type{});
+                __syncwarp();   // lane 31's spill writes are visible to the next pass
+            }
+            const bool last_a = st.flags & kMqLastA, last_b = st.flags & kMqLastB;
+            if (last_a || last_b) {
+                unsigned b = best;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) b = __vmaxs2(b, __shfl_xor_sync(0xffffffffu, b, o));
+                if (lane == 0 && seq >= 0) {
+                    if (last_a) emit_score(p, st.qa, seq, static_cast<int>(static_cast<short>(b & 0xFFFFu)));
+                    if (last_b) emit_score(p, st.qb, seq, static_cast<int>(static_cast<short>(b >> 16)));
+                }
+                if (last_a) best &= 0xFFFF0000u;
+                if (last_b) best &= 0x0000FFFFu;
+            }
+        }
+    }
+}
+
+// Two-subject mode.  kTB query rows per lane (passes of 32 * kTB rows), kW = ceil(kTB / 2)
+// words of int16 row pairs per lane and residue.  Work: the 32 slot pairs of every group in
+// [group_begin, group_end), longest groups first, kWaveBW pairs per block item.
+template <int kTB>
+__global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WaveParams p) {
+    constexpr int kBlock = kWaveBW * kWarp;
+    constexpr int kRowsB = kTB * kWarp;
+    constexpr int kW = (kTB + 1) / 2;
+    constexpr int kPStride = slice_stride<kW>();
+    extern __shared__ __align__(16) uint32_t s_sl[];   // (A + 1) x kPStride
+    __shared__ int s_item;
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warp = threadIdx.x >> 5;
+    const int my_chunk = chunk_offset<kW>(lane);
+    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kWaveBW + warp) * p.spill_stride;
+    PackedGaps k;
+    k.ngoe = pack2(-p.gaps.goe);
+    k.nge = pack2(-p.gaps.ge);
+    k.ngep = pack2(-p.gaps.gep);
+    k.floor = 0x80008000u;
+    const unsigned init_hm = k.ngoe, init_f = k.ngep;
+    const QueryDesc qd = p.queries[p.query];
+    const int passes = (qd.m + kRowsB - 1) / kRowsB;
+    const int64_t total_pairs = (p.group_end - p.group_begin) * (kGroupSeqs / 2);
+    const int bias = p.gaps.goe;   // score 0 of rows past the profile: S' = 0 + Goe
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_wave, 1u));
+        __syncthreads();
+        const int64_t first_pair = static_cast<int64_t>(s_item) * kWaveBW;
+        if (first_pair >= total_pairs) break;
+        const int64_t pi = total_pairs - 1 - (first_pair + warp);   // longest groups first
+        int id_a = -1, id_b = -1, n = 0;
+        const uint16_t* res2 = nullptr;
+        if (pi >= 0) {
+            const int64_t g = p.group_begin + pi / (kGroupSeqs / 2);
+            const int t = static_cast<int>(pi % (kGroupSeqs / 2));
+            id_a = p.perm[g * kGroupSeqs + 2 * t];
+            id_b = p.perm[g * kGroupSeqs + 2 * t + 1];
+            const int n_a = id_a >= 0 ? static_cast<int>(p.plain_off[id_a + 1] - p.plain_off[id_a]) : 0;
+            const int n_b = id_b >= 0 ? static_cast<int>(p.plain_off[id_b + 1] - p.plain_off[id_b]) : 0;
+            n = max(n_a, n_b);
+            res2 = reinterpret_cast<const uint16_t*>(p.inter + p.group_off[g] + t * 16);
+        }
+        unsigned best = 0;
+        for (int pass = 0; pass < passes; ++pass) {
+            const bool first = pass == 0, last = pass == passes - 1;
+            __syncthreads();
+            for (int v = threadIdx.x; v < p.alphabet1 * kW * kWarp; v += kBlock) {
+                const int d = v / (kW * kWarp);
+                const int rem = v - d * (kW * kWarp);
+                const int ln = rem / kW, wi = rem - ln * kW;
+                const int r0 = pass * kRowsB + ln * kTB + 2 * wi;
+                const int s0 = r0 < qd.m_pad ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + r0] : bias;
+                const int s1 = (2 * wi + 1 < kTB && r0 + 1 < qd.m_pad)
+                                   ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + r0 + 1] : bias;
+                s_sl[d * kPStride + chunk_offset<kW>(ln) + wi] =
+                    (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
+            }
+            __syncthreads();
+            if (n == 0) continue;
+            unsigned Hm[kTB], E[kTB];
+#pragma unroll
+            for (int r = 0; r < kTB; ++r) {
+                Hm[r] = init_hm;
+                E[r] = init_f;
+            }
+            unsigned hm_prev = init_hm;
+            unsigned out_hm = init_hm, out_f = init_f;
+            uint2 sp_cur = make_uint2(init_hm, init_f), sp_next = sp_cur;
+            if (!first) {
+                if (lane < n) sp_cur = reinterpret_cast<const uint2*>(spill)[lane];
+                if (32 + lane < n) sp_next = reinterpret_cast<const uint2*>(spill)[32 + lane];
+            }
+            unsigned res_next = lane == 0 ? res2[0] : 0u;
+            const int steps = n + kWarp - 1;
+            auto step = [&](const int t, const int src, auto checked, auto on_first) {
+                const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
+                const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
+                unsigned l0_hm = init_hm, l0_f = init_f;
+                if constexpr (!decltype(on_first)::value) {
+                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
+                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                }
+                const int j = t - lane;
+                const unsigned rr = res_next;
+                const int jn = j + 1;
+                if (jn >= 0 && jn < n) res_next = res2[(jn >> 3) * (kGroupChunk / 2) + (jn & 7)];
+                if (decltype(checked)::value && !(j >= 0 && j < n)) return;
+                unsigned F = lane == 0 ? l0_f : up_f;
+                unsigned d = hm_prev;
+                hm_prev = lane == 0 ? l0_hm : up_hm;
+                const uint32_t* pa = s_sl + (rr & 0xFFu) * kPStride + my_chunk;
+                const uint32_t* pb = s_sl + (rr >> 8) * kPStride + my_chunk;
+                unsigned x_prev = 0;
+#pragma unroll
+                for (int wi = 0; wi < kW; ++wi) {
+                    const unsigned wa = pa[wi], wb = pb[wi];
+                    const int r = 2 * wi;
+                    const unsigned x0 = cell2(d, Hm[r], E[r], F, __byte_perm(wa, wb, 0x5410), k);
+                    if (r + 1 < kTB) {
+                        const unsigned x1 = cell2(d, Hm[r + 1], E[r + 1], F, __byte_perm(wa, wb, 0x7632), k);
+                        best = __vimax3_s16x2(best, x0, x1);
+                    } else {
+                        x_prev = x0;
+                    }
+                }
+                if constexpr (kTB % 2 == 1) best = __vmaxs2(best, x_prev);
+                out_hm = Hm[kTB - 1];
+                out_f = F;
+                if (lane == kWarp - 1 && !last) spill[j] = make_int2(static_cast<int>(out_hm),
+                                                                     static_cast<int>(out_f));
+            };
+            auto run = [&](auto on_first) {
+                for (int tb = 0; tb < steps; tb += kWarp) {
+                    if constexpr (!decltype(on_first)::value) {
+                        if (tb > 0) {
+                            sp_cur = sp_next;
+                            if (tb + 32 + lane < n)
+                                sp_next = reinterpret_cast<const uint2*>(spill)[tb + 32 + lane];
+                        }
+                    }
+                    if (tb >= kWarp && tb + kWarp <= n) {
+                        if constexpr (kTB == 5) {
+#pragma unroll 4
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        } else {
+#pragma unroll 1
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        }
+                    } else {
+                        const int ue = min(kWarp, steps - tb);
+#pragma unroll 1
+                        for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{}, on_first);
+                    }
+                }
+            };
+            if (first)
+                run(std::true_type{});
+            else
+                run(std::false_type{});
+            __syncwarp();
+        }
+        unsigned b = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = __vmaxs2(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if (lane == 0) {
+            emit_score(p, p.query, id_a, static_cast<int>(static_cast<short>(b & 0xFFFFu)));
+            emit_score(p, p.query, id_b, static_cast<int>(static_cast<short>(b >> 16)));
+        }
+    }
+}
+
+const void* wave_ss_fn(int rows_per_lane) {
+    return rows_per_lane == 5 ? reinterpret_cast<const void*>(&k_wave_ss_i16x2<5>)
+                              : reinterpret_cast<const void*>(&k_wave_ss_i16x2<8>);
+}
+
+const void* wave_mq_fn(int rows_per_lane) {
+    return rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<8>)
+                              : reinterpret_cast<const void*>(&k_wave_mq_i16x2<16>);
+}
+
+}  // namespace
+
+int wave_warps() { return kWaveBW; }
+
+size_t wave_smem_bytes(int rows_per_lane, int alphabet1) {
+    const int stride = rows_per_lane == 8 ? slice_stride<8>() : slice_stride<16>();
+    return static_cast<size_t>(alphabet1) * stride * sizeof(uint32_t);
+}
+
+int wave_occupancy(int rows_per_lane, int alphabet1) {
+    int n = 0;
+    const size_t smem = wave_smem_bytes(rows_per_lane, alphabet1);
+    const void* fn = wave_mq_fn(rows_per_lane);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kWaveBW * kWarp, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1) {
+    const int stride = rows_per_lane == 5 ? slice_stride<3>() : slice_stride<4>();
+    return static_cast<size_t>(alphabet1) * stride * sizeof(uint32_t);
+}
+
+int wave_ss_occupancy(int rows_per_lane, int alphabet1) {
+    int n = 0;
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, alphabet1);
+    const void* fn = wave_ss_fn(rows_per_lane);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kWaveBW * kWarp, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st) {
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, p.alphabet1);
+    const void* fn = wave_ss_fn(rows_per_lane);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (rows_per_lane == 5)
+        k_wave_ss_i16x2<5><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+    else
+        k_wave_ss_i16x2<8><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_mq(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st) {
+    const size_t smem = wave_smem_bytes(rows_per_lane, p.alphabet1);
+    const void* fn = wave_mq_fn(rows_per_lane);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (rows_per_lane == 8)
+        k_wave_mq_i16x2<8><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+    else
+        k_wave_mq_i16x2<16><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace swgb

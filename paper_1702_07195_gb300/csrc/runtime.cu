@@ -73,6 +73,25 @@ bool score_profile_enabled() {
     return v && v[0] == '1';
 }
 
+// Packed int16x2 wavefront kernel for the long subjects of multi-query searches (default on).
+bool wave_enabled() {
+    const char* v = std::getenv("SWGB_WAVE");
+    return !(v && v[0] == '0');
+}
+
+// Packed int16x2 two-subject wavefront kernel for the routed groups of one-query searches
+// (default on).
+bool pair_enabled() {
+    const char* v = std::getenv("SWGB_PAIR");
+    return !(v && v[0] == '0');
+}
+
+// Blocks per SM of the two-subject wavefront kernel (0: as many as fit).
+int forced_pair_blocks_per_sm() {
+    const char* v = std::getenv("SWGB_PAIR_BLOCKS_PER_SM");
+    return v ? std::max(0, std::atoi(v)) : 0;
+}
+
 // Blocks per SM of the block int32 kernel (0: as many as fit).
 int forced_intra_blocks_per_sm() {
     const char* v = std::getenv("SWGB_INTRA_BLOCKS_PER_SM");
@@ -102,6 +121,46 @@ void destroy_plans(sw_db* db) {
         p->exec = nullptr;
     }
     db->plans.clear();
+}
+
+// Two streams of T-row strips for the kernels that pair two queries per register: queries
+// (longest first) go whole, strip by strip, to the stream with fewer strips; step k pairs strip
+// k of stream a with strip k of stream b.  Absent lanes and first strips are flagged "first"
+// (they start from the zero boundary), last strips "last" (their half's score is emitted).
+std::vector<MqStep> build_streams(const std::vector<int32_t>& m, const std::vector<int32_t>& order,
+                                  int T) {
+    std::vector<int32_t> stream[2];
+    int64_t len[2] = {0, 0};
+    for (int32_t q : order) {
+        const int32_t mq = m[static_cast<size_t>(q)];
+        if (mq == 0) continue;
+        const int x = len[0] <= len[1] ? 0 : 1;
+        stream[x].push_back(q);
+        len[x] += (mq + T - 1) / T;
+    }
+    const int64_t num_steps = std::max(len[0], len[1]);
+    std::vector<MqStep> steps(static_cast<size_t>(num_steps), MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0});
+    for (int x = 0; x < 2; ++x) {
+        int64_t k = 0;
+        for (int32_t q : stream[x]) {
+            const int32_t S = (m[static_cast<size_t>(q)] + T - 1) / T;
+            for (int32_t sidx = 0; sidx < S; ++sidx, ++k) {
+                MqStep& st = steps[static_cast<size_t>(k)];
+                uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
+                if (sidx == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
+                if (sidx == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
+                st.flags = fl;
+                if (x == 0) {
+                    st.qa = q;
+                    st.sa = sidx;
+                } else {
+                    st.qb = q;
+                    st.sb = sidx;
+                }
+            }
+        }
+    }
+    return steps;
 }
 
 // Grows the shared scratch (control block, saturation list, boundary buffers).  Cached plans
@@ -197,38 +256,36 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     P.mq = mq_enabled() && P.int16_ok && G > 0 && nonempty >= 2 &&
            db->inter_mq_occ[P.variant] > 0;
     if (P.mq) {
-        std::vector<int32_t> stream[2];
-        int64_t len[2] = {0, 0};
-        for (int32_t q : order) {
-            const int32_t mq = P.m[static_cast<size_t>(q)];
-            if (mq == 0) continue;
-            const int x = len[0] <= len[1] ? 0 : 1;
-            stream[x].push_back(q);
-            len[x] += (mq + mqT - 1) / mqT;
-        }
-        P.num_steps = static_cast<int32_t>(std::max(len[0], len[1]));
-        steps.assign(static_cast<size_t>(P.num_steps), MqStep{-1, -1, 0, 0, kMqFirstA | kMqFirstB, 0});
-        for (int x = 0; x < 2; ++x) {
-            int64_t k = 0;
-            for (int32_t q : stream[x]) {
-                const int32_t S = (P.m[static_cast<size_t>(q)] + mqT - 1) / mqT;
-                for (int32_t sidx = 0; sidx < S; ++sidx, ++k) {
-                    MqStep& st = steps[static_cast<size_t>(k)];
-                    uint32_t fl = st.flags & (x == 0 ? (kMqFirstB | kMqLastB) : (kMqFirstA | kMqLastA));
-                    if (sidx == 0) fl |= (x == 0 ? kMqFirstA : kMqFirstB);
-                    if (sidx == S - 1) fl |= (x == 0 ? kMqLastA : kMqLastB);
-                    st.flags = fl;
-                    if (x == 0) {
-                        st.qa = q;
-                        st.sa = sidx;
-                    } else {
-                        st.qb = q;
-                        st.sb = sidx;
-                    }
-                }
+        steps = build_streams(P.m, order, mqT);
+        P.num_steps = static_cast<int32_t>(steps.size());
+        P.rows_pad = round_up(static_cast<int64_t>(P.num_steps) * mqT, kQpRows);
+    }
+
+    // Long subjects of a search with two or more queries: the packed wavefront kernel pairs two
+    // queries per register against one subject (passes of 32 x 8 or 32 x 16 rows; the height
+    // with fewer padded rows, charging about 10 operations of per-step overhead per lane).
+    std::vector<MqStep> wsteps;
+    P.wave = wave_enabled() && P.int16_ok && nonempty >= 2 && !db->layout.long_ids.empty() &&
+             db->wave_occ[0] > 0 && db->wave_occ[1] > 0;
+    if (P.wave) {
+        double best_cost = 1e300;
+        for (int v = 0; v < 2; ++v) {
+            const double rows = 32.0 * kWaveRows[v];
+            double cost = 0.0;
+            for (int q = 0; q < nq; ++q)
+                cost += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (5.5 + 10.0 / kWaveRows[v]);
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                P.wave_rows = kWaveRows[v];
             }
         }
-        P.rows_pad = round_up(static_cast<int64_t>(P.num_steps) * mqT, kQpRows);
+        const int T = 32 * P.wave_rows;
+        wsteps = build_streams(P.m, order, T);
+        P.num_wsteps = static_cast<int32_t>(wsteps.size());
+        P.wrows_pad = round_up(static_cast<int64_t>(P.num_wsteps) * T, kQpRows);
+        const int occ = db->wave_occ[P.wave_rows == 8 ? 0 : 1];
+        const int64_t items = (static_cast<int64_t>(db->layout.long_ids.size()) + wave_warps() - 1) / wave_warps();
+        P.wave_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(items, static_cast<int64_t>(db->sms) * occ)));
     }
 
     // Groups whose single-warp work would outlast the rest of the search run on the int32
@@ -250,7 +307,10 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
             padded += c;
         }
         const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale;
-        const double r_intra = 3.0e12 * scale * (padded > 0 ? real / padded : 1.0);
+        // a one-query search routes its groups to the packed two-subject wavefront kernel
+        const bool pair_route = pair_enabled() && P.int16_ok && nonempty == 1 &&
+                                db->wave_ss_occ[0] > 0 && db->wave_ss_occ[1] > 0;
+        const double r_intra = (pair_route ? 4.0e12 : 3.0e12) * scale * (padded > 0 ? real / padded : 1.0);
         const int64_t warps = static_cast<int64_t>(db->sms) *
                               std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]) * W;
         double sum_m = 0, max_m = 0;
@@ -294,6 +354,27 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         P.num_items = static_cast<int64_t>(items.size());
     }
     if (P.g_split == 0) P.mq = false;
+    P.pair = pair_enabled() && P.int16_ok && nonempty == 1 && P.g_split < G &&
+             db->wave_ss_occ[0] > 0 && db->wave_ss_occ[1] > 0;
+    P.g_pair_end = P.pair ? G : P.g_split;
+    if (P.pair) {
+        double best_cost = 1e300;
+        for (int v = 0; v < 2; ++v) {
+            const double rows = 32.0 * kWaveSsRows[v];
+            double cost = 0.0;
+            for (int q = 0; q < nq; ++q)
+                cost += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (6.5 + 12.0 / kWaveSsRows[v]);
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                P.pair_rows = kWaveSsRows[v];
+            }
+        }
+        int per_sm = db->wave_ss_occ[P.pair_rows == 5 ? 0 : 1];
+        const int forced = forced_pair_blocks_per_sm();
+        if (forced > 0) per_sm = std::min(per_sm, forced);
+        const int64_t items = ((P.g_pair_end - P.g_split) * (kGroupSeqs / 2) + wave_warps() - 1) / wave_warps();
+        P.pair_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(items, static_cast<int64_t>(db->sms) * per_sm)));
+    }
 
     // Scratch shared by all plans of this database.
     P.inter_grid = db->sms * std::max(1, P.mq ? db->inter_mq_occ[P.variant]
@@ -328,7 +409,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         int per_sm = db->intra_block_occ[tb_index];
         const int bw = intra_block_warps(P.intra_rows_per_lane);
         const int64_t n_subjects = static_cast<int64_t>(db->layout.long_ids.size()) +
-                                   static_cast<int64_t>(G - P.g_split) * kGroupSeqs;
+                                   static_cast<int64_t>(G - P.g_pair_end) * kGroupSeqs;
         const int64_t block_items = (n_subjects + bw - 1) / bw * nq;
         if (bw == 4 && block_items < 8LL * db->sms * per_sm) per_sm = std::min(per_sm, 3);
         const int forced = forced_intra_blocks_per_sm();
@@ -338,8 +419,10 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     }
     const int64_t inter_slots = static_cast<int64_t>(P.inter_grid) * W;
     // per-warp pass buffers, shared by the generic and the block kernel
-    const int64_t intra_slots = std::max<int64_t>(static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp),
-                                                  static_cast<int64_t>(P.intra_block_grid) * P.intra_block_warps);
+    const int64_t intra_slots = std::max<int64_t>(
+        std::max<int64_t>(static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp),
+                          static_cast<int64_t>(P.intra_block_grid) * P.intra_block_warps),
+        static_cast<int64_t>(std::max(P.wave_grid, P.pair_grid)) * wave_warps());
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
     const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
     P.flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));
@@ -369,6 +452,10 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         CU(P.steps.ensure(steps.size()));
         CU(P.pp.ensure(static_cast<size_t>((A + 1) * P.rows_pad)));
     }
+    if (P.wave) {
+        CU(P.wsteps.ensure(wsteps.size()));
+        CU(P.wpp.ensure(static_cast<size_t>((A + 1) * P.wrows_pad)));
+    }
     std::vector<QueryDesc> descs(static_cast<size_t>(nq));
     for (int q = 0; q < nq; ++q)
         descs[static_cast<size_t>(q)] = QueryDesc{P.qp.ptr + qp_off[static_cast<size_t>(q)],
@@ -389,6 +476,9 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
                            cudaMemcpyHostToDevice, us));
     if (P.sp)
         CU(cudaMemcpyAsync(P.mt.ptr, mt.data(), sizeof(int16_t) * mt.size(), cudaMemcpyHostToDevice, us));
+    if (P.wave)
+        CU(cudaMemcpyAsync(P.wsteps.ptr, wsteps.data(), sizeof(MqStep) * wsteps.size(),
+                           cudaMemcpyHostToDevice, us));
     CU(cudaStreamSynchronize(us));
 
     const Gaps gaps{goe, ge, std::min(goe, ge)};
@@ -432,6 +522,47 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         mp.gaps = gaps;
         mp.tick = nullptr;
     }
+    if (P.wave) {
+        WaveParams& wp = P.wave_p;
+        wp.plain = db->plain_ptr;
+        wp.plain_off = db->plain_off.ptr;
+        wp.subjects = db->long_ids.ptr;
+        wp.num_subjects = static_cast<int64_t>(db->layout.long_ids.size());
+        wp.queries = P.descs.ptr;
+        wp.pp = P.wpp.ptr;
+        wp.rows_pad = P.wrows_pad;
+        wp.steps = P.wsteps.ptr;
+        wp.num_steps = P.num_wsteps;
+        wp.alphabet1 = A + 1;
+        wp.ctrl = db->ctrl.ptr;
+        wp.flags = db->flags.ptr;
+        wp.flag_cap = P.flag_cap;
+        wp.thresh = ip.thresh;
+        wp.spill = db->spill.ptr;
+        wp.spill_stride = spill_stride;
+        wp.gaps = gaps;
+    }
+    if (P.pair) {
+        WaveParams& wp = P.pair_p;
+        wp.plain_off = db->plain_off.ptr;
+        wp.queries = P.descs.ptr;
+        for (int q = 0; q < nq; ++q)
+            if (P.m[static_cast<size_t>(q)] > 0) wp.query = q;
+        wp.inter = db->inter_ptr;
+        wp.group_off = db->group_off.ptr;
+        wp.group_len = db->group_len.ptr;
+        wp.perm = db->perm.ptr;
+        wp.group_begin = P.g_split;
+        wp.group_end = P.g_pair_end;
+        wp.alphabet1 = A + 1;
+        wp.ctrl = db->ctrl.ptr;
+        wp.flags = db->flags.ptr;
+        wp.flag_cap = P.flag_cap;
+        wp.thresh = ip.thresh;
+        wp.spill = db->spill.ptr;
+        wp.spill_stride = spill_stride;
+        wp.gaps = gaps;
+    }
     IntraParams& jp = P.intra;
     jp.plain = db->plain_ptr;
     jp.plain_off = db->plain_off.ptr;
@@ -450,7 +581,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     jp.gaps = gaps;
     jp.qp_add = goe - P.qp_bias;
     jp.perm = db->perm.ptr;
-    jp.slot_begin = P.g_split * kGroupSeqs;
+    jp.slot_begin = P.g_pair_end * kGroupSeqs;
     jp.slot_end = G * kGroupSeqs;
 
     for (int q = 0; q < nq; ++q) {
@@ -493,6 +624,12 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
                        P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
     ++launches;
+    if (P.wave) {
+        CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.wsteps.ptr, P.num_wsteps, nullptr,
+                           32 * P.wave_rows, P.matrix.ptr, db->A, P.qp_bias, P.wpp.ptr,
+                           P.wrows_pad, db->ctrl.ptr, st));
+        ++launches;
+    }
     CU(record(db->ev[1], st));
     if (P.mq) {
         CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.steps.ptr, P.num_steps, nullptr,
@@ -521,11 +658,18 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     } else {
         if (jp.num_long > 0) {
             jp.mode = kIntraLong;
-            CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_rows_per_lane, P.intra_block_grid, st)
-                                      : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+            if (P.wave)
+                CU(launch_wave_mq(P.wave_p, P.wave_rows, P.wave_grid, st));
+            else
+                CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_rows_per_lane, P.intra_block_grid, st)
+                                          : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
             ++launches;
         }
-        if (P.g_split < db->layout.num_groups) {
+        if (P.pair) {
+            CU(launch_wave_ss(P.pair_p, P.pair_rows, P.pair_grid, st));
+            ++launches;
+        }
+        if (P.g_pair_end < db->layout.num_groups) {
             jp.mode = kIntraGroups;
             CU(P.intra_block_grid > 0 ? launch_intra_block(jp, P.intra_rows_per_lane, P.intra_block_grid, st)
                                       : launch_intra(jp, P.intra_grid, intra_block_threads(), st));
@@ -533,7 +677,7 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
         }
     }
     CU(record(db->ev[3], st));
-    if (P.int16_ok && (P.num_items > 0 || P.mq)) {
+    if (P.int16_ok && (P.num_items > 0 || P.mq || P.wave || P.pair)) {
         jp.mode = kIntraRescore;
         CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
         ++launches;
@@ -582,6 +726,9 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(db->no_route ? 1 : 0);
     key.push_back(forced_intra_blocks_per_sm());
     key.push_back(score_profile_enabled() ? 1 : 0);
+    key.push_back(wave_enabled() ? 1 : 0);
+    key.push_back(pair_enabled() ? 1 : 0);
+    key.push_back(forced_pair_blocks_per_sm());
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 
@@ -632,6 +779,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     db->stats.inter_block = inter_variant_warps(plan->variant) * kWarp;
     db->stats.multi_query = plan->mq ? 1 : 0;
     db->stats.score_profile = plan->sp && plan->num_items > 0 ? 1 : 0;
+    db->stats.intra_packed = plan->wave ? 1 : plan->pair ? 2 : 0;
     db->stats.graph_replay = replay ? 1 : 0;
     db->stats.variant = plan->variant;
     db->stats_pending = true;
@@ -690,7 +838,7 @@ bool db_view(const sw_db* db, DbView* v) {
 extern "C" {
 
 const char* sw_last_error(void) { return g_err.c_str(); }
-const char* sw_version(void) { return "swgb 0.2 (sm_103a)"; }
+const char* sw_version(void) { return "swgb 0.3 (sm_103a)"; }
 int64_t sw_launch_count(void) { return g_launches.load(); }
 
 sw_status sw_layout_sizes(const int64_t* offsets, int64_t num_seqs, int32_t long_cutoff,
@@ -770,6 +918,10 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
     for (int v = 0; v < 3; ++v)
         db->intra_block_occ[v] = block_off ? 0 : intra_block_occupancy(kIntraBlockRows[v], alphabet_size + 1);
+    for (int v = 0; v < 2; ++v) {
+        db->wave_occ[v] = wave_occupancy(kWaveRows[v], alphabet_size + 1);
+        db->wave_ss_occ[v] = wave_ss_occupancy(kWaveSsRows[v], alphabet_size + 1);
+    }
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
     const char* forced = std::getenv("SWGB_VARIANT");

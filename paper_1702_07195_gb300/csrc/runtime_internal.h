@@ -86,6 +86,22 @@ struct Plan {
     DevBuf<MqStep> steps;
     DevBuf<uint32_t> pp;
     InterMqParams inter_mq{};
+    // packed int16x2 wavefront kernel for the long subjects (two queries per register)
+    bool wave = false;
+    int wave_rows = 16;           // query rows per lane
+    int wave_grid = 0;
+    int32_t num_wsteps = 0;
+    int64_t wrows_pad = 0;
+    DevBuf<MqStep> wsteps;
+    DevBuf<uint32_t> wpp;
+    WaveParams wave_p{};
+    // packed int16x2 wavefront kernel for routed groups of a one-query search (two subjects
+    // per register); groups [g_split, g_pair_end) run there, [g_pair_end, G) on int32
+    bool pair = false;
+    int pair_rows = 5;
+    int pair_grid = 0;
+    int64_t g_pair_end = 0;
+    WaveParams pair_p{};
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -133,6 +149,8 @@ struct sw_db {
     int intra_occ = 0;
     int intra_block_occ[3] = {0, 0, 0};   // 5, 8 and 16 query rows per lane
     int inter_sp_occ = 0;                 // score-profile inter-task kernel
+    int wave_occ[2] = {0, 0};             // packed wavefront kernel, 8 and 16 rows per lane
+    int wave_ss_occ[2] = {0, 0};          // its two-subject mode, 5 and 8 rows per lane
     // last search
     sw_stats stats{};
     bool stats_pending = false;

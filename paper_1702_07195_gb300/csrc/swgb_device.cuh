@@ -68,8 +68,9 @@ struct Control {
     unsigned long long sweep_next;   // rescore sweep block counter
     unsigned int next_inter;         // inter-task item counter
     unsigned int next_rescore;       // saturation-list counter
-    unsigned int flag_count;         // saturated lanes seen by the inter-task kernel
+    unsigned int flag_count;         // saturated lanes seen by the int16x2 kernels
     unsigned int status;             // bit 0: a query residue code was out of range
+    unsigned int next_wave;          // packed wavefront kernel's block-item counter
 };
 
 struct Gaps {
@@ -166,6 +167,48 @@ struct IntraParams {
     const int32_t* perm;        // kIntraGroups: group slot -> sequence id (-1 filler)
     int64_t slot_begin, slot_end;
 };
+
+// Packed int16x2 intra-task wavefront kernel (k_wave.cu).  Two int16 lanes per register:
+//  * two-query mode (queries != two-subject): one subject per warp against two streams of
+//    query passes (pass k of stream a in the low lanes, of stream b in the high lanes; the
+//    pass structure is an MqStep list with rows_per_step = 32 x rows per lane), scores from
+//    the paired profile pp;
+//  * two-subject mode: one query, the subjects in slots 2t and 2t + 1 of an interleaved group
+//    per warp, scores from the query profile qp (two lookups packed by a byte permute).
+struct WaveParams {
+    const uint8_t* plain;       // two-query mode: subjects in original order
+    const int64_t* plain_off;
+    const int32_t* subjects;    // two-query mode: subject ids, longest first
+    int64_t num_subjects;
+    const QueryDesc* queries;   // score rows (and the profile in two-subject mode)
+    const uint32_t* pp;         // two-query mode: pp[d * rows_pad + k * rows_per_step + r]
+    int64_t rows_pad;
+    const MqStep* steps;
+    int32_t num_steps;
+    int32_t query;              // two-subject mode: the query slot
+    const uint8_t* inter;       // two-subject mode: interleaved groups [group_begin, group_end)
+    const int64_t* group_off;
+    const int32_t* group_len;
+    const int32_t* perm;
+    int64_t group_begin, group_end;
+    int32_t alphabet1;
+    Control* ctrl;
+    FlagEntry* flags;
+    uint32_t flag_cap;
+    int32_t thresh;             // int16 saturation threshold: 32767 - max(0, max SM)
+    int2* spill;                // per resident warp: pass-boundary row, one int2 per column
+    int64_t spill_stride;
+    Gaps gaps;
+};
+constexpr int kWaveRows[2] = {8, 16};   // query rows per lane of the two-query variants
+int wave_warps();
+size_t wave_smem_bytes(int rows_per_lane, int alphabet1);
+int wave_occupancy(int rows_per_lane, int alphabet1);
+cudaError_t launch_wave_mq(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st);
+constexpr int kWaveSsRows[2] = {5, 8};  // query rows per lane of the two-subject variants
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1);
+int wave_ss_occupancy(int rows_per_lane, int alphabet1);
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st);
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_build_qp(const uint8_t* d_queries, const int64_t* d_qoff, int32_t nq,

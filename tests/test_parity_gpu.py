@@ -136,8 +136,10 @@ def test_saturating_hits_rescored_exactly(sw, flag_cap, monkeypatch):
 @pytest.mark.parametrize("block", ["1", "0"])
 def test_long_subjects_intra_kernel(sw, block, monkeypatch):
     """Subjects above the cutoff on the int32 intra-task kernel: the block-shared-profile
-    variant (default) and the per-warp variant (SWGB_INTRA_BLOCK=0)."""
+    variant (default) and the per-warp variant (SWGB_INTRA_BLOCK=0); the packed int16x2
+    wavefront kernel, which a batch of queries would otherwise take, is switched off."""
     monkeypatch.setenv("SWGB_INTRA_BLOCK", block)
+    monkeypatch.setenv("SWGB_WAVE", "0")
     rng = np.random.default_rng(9)
     lens = np.concatenate([rng.integers(1, 300, size=120), rng.integers(1000, 2600, size=9), [4097]])
     db = w.database_from_lengths(rng, lens)
