@@ -34,6 +34,7 @@
 // like the inter-task kernels' lanes.  The pass-boundary row (H - Goe, F) of each column goes
 // through a per-warp global buffer as one int2 of packed pairs, written by lane 31 and read by
 // lane 0 of the next pass, 32 columns at a time.
+#include <algorithm>
 #include <type_traits>
 
 #include "slice_layout.cuh"
@@ -64,6 +65,36 @@ __device__ __forceinline__ unsigned cell2(unsigned& d, unsigned& hm, unsigned& e
     e = __viaddmax_s16x2(e, k.nge, hm);                      // E of the next column
     f = __viaddmax_s16x2(f, k.ngep, xm);                     // F of the next row
     return x;
+}
+
+// One column step of a lane's kTB rows on both halves, in two phases: first X (and X - Goe)
+// of every row from the previous column's state -- row r's diagonal is row r - 1's H - Goe
+// of the previous column, still in Hm[r - 1] (d for row 0) -- then the F chain down the rows,
+// which overwrites Hm and E in place.  Same operations as kTB calls of cell2, without the
+// register rotation that keeping the old Hm[r] for the next row needs there.
+template <int kTB>
+__device__ __forceinline__ void column2(unsigned (&Hm)[kTB], unsigned (&E)[kTB], unsigned& F,
+                                        const unsigned d, const unsigned (&sc)[kTB],
+                                        const PackedGaps& k, unsigned& best) {
+    unsigned xm[kTB];
+#pragma unroll
+    for (int r = 0; r < kTB; r += 2) {
+        const unsigned xa = __viaddmax_s16x2_relu(r == 0 ? d : Hm[r - 1], sc[r], E[r]);
+        xm[r] = __viaddmax_s16x2(xa, k.ngoe, k.floor);
+        if (r + 1 < kTB) {
+            const unsigned xb = __viaddmax_s16x2_relu(Hm[r], sc[r + 1], E[r + 1]);
+            xm[r + 1] = __viaddmax_s16x2(xb, k.ngoe, k.floor);
+            best = __vimax3_s16x2(best, xa, xb);
+        } else {
+            best = __vmaxs2(best, xa);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kTB; ++r) {
+        Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm[r]);      // H - Goe = max(F, X) - Goe
+        E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);     // E of the next column
+        F = __viaddmax_s16x2(F, k.ngep, xm[r]);          // F of the next row
+    }
 }
 
 __device__ __forceinline__ void emit_score(const WaveParams& p, int q, int id, int v) {
@@ -176,19 +207,19 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WavePar
                     if (j + 1 >= 0 && j + 1 < n) res_next = subj[j + 1];
                     if (decltype(checked)::value && !(j >= 0 && j < n)) return;
                     unsigned F = lane == 0 ? l0_f : up_f;     // F(r0, j)
-                    unsigned d = hm_prev;                      // (H - Goe)(r0 - 1, j - 1)
+                    const unsigned d = hm_prev;                // (H - Goe)(r0 - 1, j - 1)
                     hm_prev = lane == 0 ? l0_hm : up_hm;       // (H - Goe)(r0 - 1, j)
                     const uint4* prow = reinterpret_cast<const uint4*>(s_pp + res * kPStride + my_chunk);
+                    unsigned sc[kTB];
 #pragma unroll
                     for (int r4 = 0; r4 < kTB; r4 += 4) {
                         const uint4 sv = prow[r4 >> 2];
-                        const unsigned x0 = cell2(d, Hm[r4], E[r4], F, sv.x, k);
-                        const unsigned x1 = cell2(d, Hm[r4 + 1], E[r4 + 1], F, sv.y, k);
-                        best = __vimax3_s16x2(best, x0, x1);
-                        const unsigned x2 = cell2(d, Hm[r4 + 2], E[r4 + 2], F, sv.z, k);
-                        const unsigned x3 = cell2(d, Hm[r4 + 3], E[r4 + 3], F, sv.w, k);
-                        best = __vimax3_s16x2(best, x2, x3);
+                        sc[r4] = sv.x;
+                        sc[r4 + 1] = sv.y;
+                        sc[r4 + 2] = sv.z;
+                        sc[r4 + 3] = sv.w;
                     }
+                    column2<kTB>(Hm, E, F, d, sc, k, best);
                     out_hm = Hm[kTB - 1];
                     out_f = F;
                     if (lane == kWarp - 1 && write) spill[j] = make_int2(static_cast<int>(out_hm),
@@ -238,20 +269,39 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WavePar
 }
 
 // Two-subject mode.  kTB query rows per lane (passes of 32 * kTB rows), kW = ceil(kTB / 2)
-// words of int16 row pairs per lane and residue.  Work: the 32 slot pairs of every group in
-// [group_begin, group_end), longest groups first, kWaveBW pairs per block item.
+// words of int16 row pairs per lane and residue.  The whole query profile (every pass) sits in
+// shared memory, staged once per block, and each warp copies the residue pairs of its current
+// slot pair into its own shared-memory buffer, so the warps of a block are independent: each
+// takes one slot pair at a time from a work counter, with no block-wide synchronisation, and a
+// step reads only shared memory (the residues of the next column, then their profile words).
+//
+// Every step of the wavefront runs on all 32 lanes.  A lane whose column lies before the
+// subject (j < 0) or past its end (j >= n) computes a column of the dummy code (score 0) from
+// the boundary values: before column 0 that leaves H at 0 and only lowers E and F, which stay
+// at or below 0 and reach H only through max(0, ...) (and never below -Goe - Ge); past the end
+// every H is bounded by a real cell.  So the scores are exact and no lane branches.
+//
+// Work: the 32 slot pairs of every group in [group_begin, group_end), numbered longest first.
+// The first `long_pairs` of them form a separate queue served in a first phase by the first
+// kSsLongWarps warps of blocks [0, long_blocks) while the block's other warps wait at a
+// barrier, so that the wavefronts of the longest subjects, which set the length of a search on
+// a small database, share their SM sub-partitions with fewer warps.  Then every warp serves the
+// rest, longest first.
+constexpr int kSsBW = 8;          // warps per block
+constexpr int kSsBlocksPerSM = 2;
+constexpr int kSsLongWarps = 4;   // warps of a long block that run the first phase
+constexpr int kResPad = 32;       // dummy columns kept before column 0 in a residue buffer
+
 template <int kTB>
-__global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WaveParams p) {
-    constexpr int kBlock = kWaveBW * kWarp;
+__global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2(const WaveParams p) {
     constexpr int kRowsB = kTB * kWarp;
     constexpr int kW = (kTB + 1) / 2;
     constexpr int kPStride = slice_stride<kW>();
-    extern __shared__ __align__(16) uint32_t s_sl[];   // (A + 1) x kPStride
-    __shared__ int s_item;
+    extern __shared__ __align__(16) uint32_t s_sl[];   // passes x (A + 1) x kPStride, residues
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
     const int my_chunk = chunk_offset<kW>(lane);
-    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kWaveBW + warp) * p.spill_stride;
+    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kSsBW + warp) * p.spill_stride;
     PackedGaps k;
     k.ngoe = pack2(-p.gaps.goe);
     k.nge = pack2(-p.gaps.ge);
@@ -260,45 +310,72 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WavePar
     const unsigned init_hm = k.ngoe, init_f = k.ngep;
     const QueryDesc qd = p.queries[p.query];
     const int passes = (qd.m + kRowsB - 1) / kRowsB;
+    const int slice_words = p.alphabet1 * kPStride;
     const int64_t total_pairs = (p.group_end - p.group_begin) * (kGroupSeqs / 2);
     const int bias = p.gaps.goe;   // score 0 of rows past the profile: S' = 0 + Goe
+    const uint16_t dummy2 = static_cast<uint16_t>((p.alphabet1 - 1) * 0x0101);
+    // residue buffer of this warp: column c of the pair at index c + kResPad
+    const int res_stride = wave_ss_res_stride(p.max_group_len);
+    uint16_t* rbuf = reinterpret_cast<uint16_t*>(s_sl + passes * slice_words) + warp * res_stride;
 
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&p.ctrl->next_wave, 1u));
-        __syncthreads();
-        const int64_t first_pair = static_cast<int64_t>(s_item) * kWaveBW;
-        if (first_pair >= total_pairs) break;
-        const int64_t pi = total_pairs - 1 - (first_pair + warp);   // longest groups first
-        int id_a = -1, id_b = -1, n = 0;
-        const uint16_t* res2 = nullptr;
-        if (pi >= 0) {
-            const int64_t g = p.group_begin + pi / (kGroupSeqs / 2);
-            const int t = static_cast<int>(pi % (kGroupSeqs / 2));
-            id_a = p.perm[g * kGroupSeqs + 2 * t];
-            id_b = p.perm[g * kGroupSeqs + 2 * t + 1];
-            const int n_a = id_a >= 0 ? static_cast<int>(p.plain_off[id_a + 1] - p.plain_off[id_a]) : 0;
-            const int n_b = id_b >= 0 ? static_cast<int>(p.plain_off[id_b + 1] - p.plain_off[id_b]) : 0;
-            n = max(n_a, n_b);
-            res2 = reinterpret_cast<const uint16_t*>(p.inter + p.group_off[g] + t * 16);
+    // The whole query profile (Section 4.3), built here from the query and the matrix:
+    // pass, residue d, lane chunk, word w = rows (2w, 2w + 1) of the lane, each S'(q_i, d) =
+    // SM(q_i, d) + Goe; the dummy code and rows past the query score 0 (S' = Goe).  A query
+    // residue outside the alphabet sets status bit 0 (reported by the host after the search).
+    const int A = p.alphabet1 - 1;
+    const uint8_t* qres = p.qres + p.qres_off[p.query];
+    auto score = [&](int row, int d) -> int {
+        if (row >= qd.m || d >= A) return bias;
+        const int code = qres[row];
+        if (code >= A) {
+            if (d == 0) atomicOr(&p.ctrl->status, 1u);
+            return bias;
         }
+        return p.matrix[code * A + d] + bias;
+    };
+    for (int v = threadIdx.x; v < passes * p.alphabet1 * kW * kWarp; v += blockDim.x) {
+        const int ps = v / (p.alphabet1 * kW * kWarp);
+        const int rem0 = v - ps * (p.alphabet1 * kW * kWarp);
+        const int d = rem0 / (kW * kWarp);
+        const int rem = rem0 - d * (kW * kWarp);
+        const int ln = rem / kW, wi = rem - ln * kW;
+        const int r0 = ps * kRowsB + ln * kTB + 2 * wi;
+        const int s0 = score(r0, d);
+        const int s1 = 2 * wi + 1 < kTB ? score(r0 + 1, d) : bias;
+        s_sl[ps * slice_words + d * kPStride + chunk_offset<kW>(ln) + wi] =
+            (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
+    }
+    __syncthreads();
+
+    // One slot pair (pair index pi, 0 = the longest) over every pass.
+    auto align_pair = [&](const int64_t pi) {
+        const int64_t g = p.group_end - 1 - pi / (kGroupSeqs / 2);
+        const int t = kGroupSeqs / 2 - 1 - static_cast<int>(pi % (kGroupSeqs / 2));
+        const int id_a = p.perm[g * kGroupSeqs + 2 * t];
+        const int id_b = p.perm[g * kGroupSeqs + 2 * t + 1];
+        const int n_a = id_a >= 0 ? static_cast<int>(p.plain_off[id_a + 1] - p.plain_off[id_a]) : 0;
+        const int n_b = id_b >= 0 ? static_cast<int>(p.plain_off[id_b + 1] - p.plain_off[id_b]) : 0;
+        const int n = max(n_a, n_b);
+        // residue pairs of columns [0, n rounded up to 8) from the interleaved group (16 bytes
+        // = 8 columns per load; past each subject's end the layout holds the dummy code), the
+        // dummy pair elsewhere in [-kResPad, n + kWarp + 1)
+        const uint4* src = reinterpret_cast<const uint4*>(p.inter + p.group_off[g] + t * 16);
+        const int chunks = (n + 7) >> 3;
+        __syncwarp();   // the previous pair's steps have read the buffer
+        // uniform trip counts (predicated bodies): the warp stays converged
+        for (int c0 = 0; c0 < chunks; c0 += kWarp) {
+            const int c = c0 + lane;
+            if (c < chunks)
+                *reinterpret_cast<uint4*>(rbuf + kResPad + 8 * c) = src[static_cast<int64_t>(c) * (kGroupChunk / 16)];
+        }
+        rbuf[lane] = dummy2;                                  // columns [-kResPad, 0)
+        for (int c0 = kResPad + 8 * chunks; c0 < kResPad + n + kWarp + 2; c0 += kWarp)
+            if (c0 + lane < kResPad + n + kWarp + 2) rbuf[c0 + lane] = dummy2;
+        __syncwarp();
+        const uint16_t* rcol = rbuf + kResPad - lane;   // rcol[t] = residues of column t - lane
         unsigned best = 0;
-        for (int pass = 0; pass < passes; ++pass) {
-            const bool first = pass == 0, last = pass == passes - 1;
-            __syncthreads();
-            for (int v = threadIdx.x; v < p.alphabet1 * kW * kWarp; v += kBlock) {
-                const int d = v / (kW * kWarp);
-                const int rem = v - d * (kW * kWarp);
-                const int ln = rem / kW, wi = rem - ln * kW;
-                const int r0 = pass * kRowsB + ln * kTB + 2 * wi;
-                const int s0 = r0 < qd.m_pad ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + r0] : bias;
-                const int s1 = (2 * wi + 1 < kTB && r0 + 1 < qd.m_pad)
-                                   ? qd.qp[static_cast<int64_t>(d) * qd.m_pad + r0 + 1] : bias;
-                s_sl[d * kPStride + chunk_offset<kW>(ln) + wi] =
-                    (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
-            }
-            __syncthreads();
-            if (n == 0) continue;
+        for (int pass = 0; n > 0 && pass < passes; ++pass) {
+            const uint32_t* sl = s_sl + pass * slice_words + my_chunk;
             unsigned Hm[kTB], E[kTB];
 #pragma unroll
             for (int r = 0; r < kTB; ++r) {
@@ -308,50 +385,68 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WavePar
             unsigned hm_prev = init_hm;
             unsigned out_hm = init_hm, out_f = init_f;
             uint2 sp_cur = make_uint2(init_hm, init_f), sp_next = sp_cur;
-            if (!first) {
+            if (pass > 0) {
                 if (lane < n) sp_cur = reinterpret_cast<const uint2*>(spill)[lane];
                 if (32 + lane < n) sp_next = reinterpret_cast<const uint2*>(spill)[32 + lane];
             }
-            unsigned res_next = lane == 0 ? res2[0] : 0u;
+            // Pipeline: at step t a lane holds the profile words of its column (loaded during
+            // step t - 1) and loads its next column's residues, then their words.
+            unsigned wa[kW], wb[kW];
+            {
+                const unsigned r0 = rcol[0];
+#pragma unroll
+                for (int wi = 0; wi < kW; ++wi) {
+                    wa[wi] = sl[(r0 & 0xFFu) * kPStride + wi];
+                    wb[wi] = sl[(r0 >> 8) * kPStride + wi];
+                }
+            }
             const int steps = n + kWarp - 1;
-            auto step = [&](const int t, const int src, auto checked, auto on_first) {
+            auto step = [&](const int t, const int src_lane, auto on_first, auto write) {
                 const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                 const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
                 unsigned l0_hm = init_hm, l0_f = init_f;
                 if constexpr (!decltype(on_first)::value) {
-                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
-                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
+                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src_lane);
+                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src_lane);
                 }
-                const int j = t - lane;
-                const unsigned rr = res_next;
-                const int jn = j + 1;
-                if (jn >= 0 && jn < n) res_next = res2[(jn >> 3) * (kGroupChunk / 2) + (jn & 7)];
-                if (decltype(checked)::value && !(j >= 0 && j < n)) return;
-                unsigned F = lane == 0 ? l0_f : up_f;
-                unsigned d = hm_prev;
-                hm_prev = lane == 0 ? l0_hm : up_hm;
-                const uint32_t* pa = s_sl + (rr & 0xFFu) * kPStride + my_chunk;
-                const uint32_t* pb = s_sl + (rr >> 8) * kPStride + my_chunk;
-                unsigned x_prev = 0;
+                unsigned ca[kW], cb[kW];
+                const unsigned rn = rcol[t + 1];
 #pragma unroll
                 for (int wi = 0; wi < kW; ++wi) {
-                    const unsigned wa = pa[wi], wb = pb[wi];
-                    const int r = 2 * wi;
-                    const unsigned x0 = cell2(d, Hm[r], E[r], F, __byte_perm(wa, wb, 0x5410), k);
-                    if (r + 1 < kTB) {
-                        const unsigned x1 = cell2(d, Hm[r + 1], E[r + 1], F, __byte_perm(wa, wb, 0x7632), k);
-                        best = __vimax3_s16x2(best, x0, x1);
-                    } else {
-                        x_prev = x0;
-                    }
+                    ca[wi] = wa[wi];
+                    cb[wi] = wb[wi];
+                    wa[wi] = sl[(rn & 0xFFu) * kPStride + wi];   // step t + 1
+                    wb[wi] = sl[(rn >> 8) * kPStride + wi];
                 }
-                if constexpr (kTB % 2 == 1) best = __vmaxs2(best, x_prev);
+                unsigned F = lane == 0 ? l0_f : up_f;
+                const unsigned d = hm_prev;
+                hm_prev = lane == 0 ? l0_hm : up_hm;
+                unsigned sc[kTB];
+#pragma unroll
+                for (int wi = 0; wi < kW; ++wi) {
+                    sc[2 * wi] = __byte_perm(ca[wi], cb[wi], 0x5410);
+                    if (2 * wi + 1 < kTB) sc[2 * wi + 1] = __byte_perm(ca[wi], cb[wi], 0x7632);
+                }
+                column2<kTB>(Hm, E, F, d, sc, k, best);
                 out_hm = Hm[kTB - 1];
                 out_f = F;
-                if (lane == kWarp - 1 && !last) spill[j] = make_int2(static_cast<int>(out_hm),
-                                                                     static_cast<int>(out_f));
+                if constexpr (decltype(write)::value) {
+                    const int j = t - lane;
+                    if (lane == kWarp - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n))
+                        spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
+                }
             };
-            auto run = [&](auto on_first) {
+            auto run = [&](auto on_first, auto write) {
+                if constexpr (decltype(on_first)::value) {
+                    // constant lane-0 boundary: no 32-step blocks; an extra step past the end
+                    // (every lane on a dummy column) is harmless
+#pragma unroll 1
+                    for (int t = 0; t < steps; t += 2) {
+                        step(t, 0, on_first, write);
+                        step(t + 1, 0, on_first, write);
+                    }
+                    return;
+                }
                 for (int tb = 0; tb < steps; tb += kWarp) {
                     if constexpr (!decltype(on_first)::value) {
                         if (tb > 0) {
@@ -360,25 +455,28 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WavePar
                                 sp_next = reinterpret_cast<const uint2*>(spill)[tb + 32 + lane];
                         }
                     }
-                    if (tb >= kWarp && tb + kWarp <= n) {
-                        if constexpr (kTB == 5) {
-#pragma unroll 4
-                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
-                        } else {
-#pragma unroll 1
-                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
-                        }
+                    const int ue = min(kWarp, steps - tb);
+                    if (ue == kWarp) {
+#pragma unroll 2
+                        for (int u = 0; u < kWarp; ++u) step(tb + u, u, on_first, write);
                     } else {
-                        const int ue = min(kWarp, steps - tb);
 #pragma unroll 1
-                        for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{}, on_first);
+                        for (int u = 0; u < ue; ++u) step(tb + u, u, on_first, write);
                     }
                 }
             };
-            if (first)
-                run(std::true_type{});
-            else
-                run(std::false_type{});
+            const bool last = pass == passes - 1;
+            if (pass == 0) {
+                if (last)
+                    run(std::true_type{}, std::false_type{});
+                else
+                    run(std::true_type{}, std::true_type{});
+            } else {
+                if (last)
+                    run(std::false_type{}, std::false_type{});
+                else
+                    run(std::false_type{}, std::true_type{});
+            }
             __syncwarp();
         }
         unsigned b = best;
@@ -388,6 +486,28 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_ss_i16x2(const WavePar
             emit_score(p, p.query, id_a, static_cast<int>(static_cast<short>(b & 0xFFFFu)));
             emit_score(p, p.query, id_b, static_cast<int>(static_cast<short>(b >> 16)));
         }
+        __syncwarp();
+    };
+
+    const int64_t long_pairs = min(p.long_pairs, total_pairs);
+    if (static_cast<int>(blockIdx.x) < p.long_blocks) {
+        if (warp < kSsLongWarps) {
+            for (;;) {
+                unsigned it = 0;
+                if (lane == 0) it = atomicAdd(&p.ctrl->next_wave_long, 1u);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= long_pairs) break;
+                align_pair(it);
+            }
+        }
+        __syncthreads();   // the block's other warps wait here: one active warp per sub-partition
+    }
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(&p.ctrl->next_wave, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (long_pairs + it >= total_pairs) break;
+        align_pair(long_pairs + it);
     }
 }
 
@@ -420,31 +540,40 @@ int wave_occupancy(int rows_per_lane, int alphabet1) {
     return n;
 }
 
-size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1) {
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len) {
     const int stride = rows_per_lane == 5 ? slice_stride<3>() : slice_stride<4>();
-    return static_cast<size_t>(alphabet1) * stride * sizeof(uint32_t);
+    const int passes = std::max(1, (m + 32 * rows_per_lane - 1) / (32 * rows_per_lane));
+    return static_cast<size_t>(passes) * alphabet1 * stride * sizeof(uint32_t) +
+           static_cast<size_t>(kSsBW) * wave_ss_res_stride(max_group_len) * sizeof(uint16_t);
 }
 
-int wave_ss_occupancy(int rows_per_lane, int alphabet1) {
-    int n = 0;
-    const size_t smem = wave_ss_smem_bytes(rows_per_lane, alphabet1);
+int wave_ss_warps() { return kSsBW; }
+int wave_ss_blocks_per_sm() { return kSsBlocksPerSM; }
+int wave_ss_long_warps() { return kSsLongWarps; }
+
+bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem) {
+    if (m <= 0) return false;
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, alphabet1, m, max_group_len);
+    if (smem * kSsBlocksPerSM > static_cast<size_t>(max_smem)) return false;
     const void* fn = wave_ss_fn(rows_per_lane);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kWaveBW * kWarp, smem) != cudaSuccess)
-        return 0;
-    return n;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
+        return false;
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kSsBW * kWarp, smem) == cudaSuccess &&
+           n >= kSsBlocksPerSM;
 }
 
-cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st) {
-    const size_t smem = wave_ss_smem_bytes(rows_per_lane, p.alphabet1);
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int m, int grid, cudaStream_t st) {
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, p.alphabet1, m, p.max_group_len);
     const void* fn = wave_ss_fn(rows_per_lane);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     if (rows_per_lane == 5)
-        k_wave_ss_i16x2<5><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+        k_wave_ss_i16x2<5><<<grid, kSsBW * kWarp, smem, st>>>(p);
     else
-        k_wave_ss_i16x2<8><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+        k_wave_ss_i16x2<8><<<grid, kSsBW * kWarp, smem, st>>>(p);
     return cudaGetLastError();
 }
 

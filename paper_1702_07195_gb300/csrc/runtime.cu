@@ -86,12 +86,6 @@ bool pair_enabled() {
     return !(v && v[0] == '0');
 }
 
-// Blocks per SM of the two-subject wavefront kernel (0: as many as fit).
-int forced_pair_blocks_per_sm() {
-    const char* v = std::getenv("SWGB_PAIR_BLOCKS_PER_SM");
-    return v ? std::max(0, std::atoi(v)) : 0;
-}
-
 // Blocks per SM of the block int32 kernel (0: as many as fit).
 int forced_intra_blocks_per_sm() {
     const char* v = std::getenv("SWGB_INTRA_BLOCKS_PER_SM");
@@ -177,6 +171,12 @@ sw_status ensure_scratch(sw_db* db, size_t flag_cap, size_t bnd_elems, size_t sp
     CU(db->bnd.ensure(std::max(bnd_elems, db->bnd.cap)));
     CU(db->spill.ensure(std::max(spill_elems, db->spill.cap)));
     return SW_OK;
+}
+
+int64_t max_m_of(const Plan& P) {
+    int64_t mx = 0;
+    for (int32_t m : P.m) mx = std::max<int64_t>(mx, m);
+    return mx;
 }
 
 // Builds the launch plan of one search shape: host tables, device copies, kernel parameters.
@@ -291,6 +291,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // Groups whose single-warp work would outlast the rest of the search run on the int32
     // intra-task kernel instead (one warp per pair): pick the split that minimises
     // max(inter work / rate, longest inter item) + routed work / intra rate.
+    int64_t max_m_q = 0;
+    for (int q = 0; q < nq; ++q) max_m_q = std::max<int64_t>(max_m_q, P.m[static_cast<size_t>(q)]);
     {
         const double scale = db->sms / 152.0;
         // the int32 kernel computes whole passes of 32 x (5, 8 or 16) rows: charge it for the
@@ -309,7 +311,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         const double r_inter = (P.mq ? 6.5e12 : 5.4e12) * scale;
         // a one-query search routes its groups to the packed two-subject wavefront kernel
         const bool pair_route = pair_enabled() && P.int16_ok && nonempty == 1 &&
-                                db->wave_ss_occ[0] > 0 && db->wave_ss_occ[1] > 0;
+                                wave_ss_fits(5, A + 1, static_cast<int>(std::max<int64_t>(1, max_m_q)),
+                                             db->layout.max_group_len, db->max_smem);
         const double r_intra = (pair_route ? 4.0e12 : 3.0e12) * scale * (padded > 0 ? real / padded : 1.0);
         const int64_t warps = static_cast<int64_t>(db->sms) *
                               std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]) * W;
@@ -354,26 +357,52 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         P.num_items = static_cast<int64_t>(items.size());
     }
     if (P.g_split == 0) P.mq = false;
-    P.pair = pair_enabled() && P.int16_ok && nonempty == 1 && P.g_split < G &&
-             db->wave_ss_occ[0] > 0 && db->wave_ss_occ[1] > 0;
-    P.g_pair_end = P.pair ? G : P.g_split;
-    if (P.pair) {
+    // One query with routed groups: the packed two-subject wavefront kernel, if its whole
+    // profile fits in shared memory (passes of 160 or 256 rows, the cheaper padded height).
+    P.pair = false;
+    if (pair_enabled() && P.int16_ok && nonempty == 1 && P.g_split < G) {
         double best_cost = 1e300;
         for (int v = 0; v < 2; ++v) {
-            const double rows = 32.0 * kWaveSsRows[v];
-            double cost = 0.0;
-            for (int q = 0; q < nq; ++q)
-                cost += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (6.5 + 12.0 / kWaveSsRows[v]);
+            const int rows_l = kWaveSsRows[v];
+            if (!wave_ss_fits(rows_l, A + 1, static_cast<int>(max_m_q), db->layout.max_group_len,
+                              db->max_smem))
+                continue;
+            const double rows = 32.0 * rows_l;
+            const double cost = std::ceil(max_m_q / rows) * rows * (6.5 + 12.0 / rows_l);
             if (cost < best_cost * 0.999) {
                 best_cost = cost;
-                P.pair_rows = kWaveSsRows[v];
+                P.pair_rows = rows_l;
+                P.pair = true;
             }
         }
-        int per_sm = db->wave_ss_occ[P.pair_rows == 5 ? 0 : 1];
-        const int forced = forced_pair_blocks_per_sm();
-        if (forced > 0) per_sm = std::min(per_sm, forced);
-        const int64_t items = ((P.g_pair_end - P.g_split) * (kGroupSeqs / 2) + wave_warps() - 1) / wave_warps();
-        P.pair_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(items, static_cast<int64_t>(db->sms) * per_sm)));
+    }
+    P.g_pair_end = P.pair ? G : P.g_split;
+    if (P.pair) {
+        P.pair_grid = db->sms * wave_ss_blocks_per_sm();
+        // Longest slot pairs first, in a phase of their own with one active warp per SM
+        // sub-partition.  Model: a step costs c_step = 2 x (kTB x 6.5 + 8) ALU-pipe clocks (half
+        // an instruction per clock); the bulk, spread over every sub-partition at ~70 % of the
+        // pipe, takes t_bulk; in the bulk phase four warps share a sub-partition, so a pair
+        // whose wavefront would then outlast t_bulk goes to the first phase.
+        const int rows_l = P.pair_rows;
+        const double c_step = 2.0 * (rows_l * 6.5 + 8.0);
+        const double passes = std::ceil(static_cast<double>(max_m_q) / (32.0 * rows_l));
+        double steps_all = 0.0;
+        for (int64_t g = P.g_split; g < G; ++g)
+            steps_all += 32.0 * (db->layout.group_len[static_cast<size_t>(g)] + 31.0) * passes;
+        const double t_bulk = steps_all * c_step / (4.0 * db->sms) / 0.7;
+        int64_t long_groups = 0;
+        for (int64_t g = G - 1; g >= P.g_split; --g) {
+            const double span4 = (db->layout.group_len[static_cast<size_t>(g)] + 31.0) * passes * 4.0 * c_step / 0.7;
+            if (span4 <= t_bulk) break;
+            ++long_groups;
+        }
+        const char* ev = std::getenv("SWGB_LONG_PAIRS");
+        int64_t long_pairs = long_groups * (kGroupSeqs / 2);
+        if (ev) long_pairs = std::max<int64_t>(0, std::atoll(ev));
+        P.pair_long_pairs = long_pairs;
+        P.pair_long_blocks = static_cast<int>(std::min<int64_t>(
+            db->sms / 2, (long_pairs + wave_ss_long_warps() - 1) / wave_ss_long_warps()));
     }
 
     // Scratch shared by all plans of this database.
@@ -422,7 +451,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     const int64_t intra_slots = std::max<int64_t>(
         std::max<int64_t>(static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp),
                           static_cast<int64_t>(P.intra_block_grid) * P.intra_block_warps),
-        static_cast<int64_t>(std::max(P.wave_grid, P.pair_grid)) * wave_warps());
+        std::max<int64_t>(static_cast<int64_t>(P.wave_grid) * wave_warps(),
+                          static_cast<int64_t>(P.pair_grid) * wave_ss_warps()));
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
     const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
     P.flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));
@@ -554,6 +584,11 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         wp.perm = db->perm.ptr;
         wp.group_begin = P.g_split;
         wp.group_end = P.g_pair_end;
+        wp.long_pairs = P.pair_long_pairs;
+        wp.max_group_len = db->layout.max_group_len;
+        wp.qres_off = P.qoff.ptr;
+        wp.matrix = P.matrix.ptr;
+        wp.long_blocks = P.pair_long_blocks;
         wp.alphabet1 = A + 1;
         wp.ctrl = db->ctrl.ptr;
         wp.flags = db->flags.ptr;
@@ -621,8 +656,21 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     for (int q = 0; q < P.nq; ++q)   // empty queries score 0 everywhere
         if (P.m[static_cast<size_t>(q)] == 0 && N > 0)
             CU(cudaMemsetAsync(P.d_scores + static_cast<int64_t>(q) * N, 0, sizeof(int32_t) * N, st));
-    CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
-                       P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
+    // A one-query search that runs only the two-subject wavefront kernel (it builds its own
+    // profile) needs the int16 query profile for the rescore alone: build it on a side branch
+    // that joins before the rescore, off the critical path.
+    const bool qp_side = P.pair && P.num_items == 0 && db->layout.long_ids.empty() &&
+                         P.g_pair_end == db->layout.num_groups && !P.wave;
+    if (qp_side) {
+        CU(cudaEventRecord(db->fork_ev, st));
+        CU(cudaStreamWaitEvent(db->side_stream, db->fork_ev, 0));
+        CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
+                           P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, db->side_stream));
+        CU(cudaEventRecord(db->join_ev, db->side_stream));
+    } else {
+        CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
+                           P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
+    }
     ++launches;
     if (P.wave) {
         CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.wsteps.ptr, P.num_wsteps, nullptr,
@@ -666,7 +714,9 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
             ++launches;
         }
         if (P.pair) {
-            CU(launch_wave_ss(P.pair_p, P.pair_rows, P.pair_grid, st));
+            WaveParams pp = P.pair_p;
+            pp.qres = d_queries;
+            CU(launch_wave_ss(pp, P.pair_rows, static_cast<int>(max_m_of(P)), P.pair_grid, st));
             ++launches;
         }
         if (P.g_pair_end < db->layout.num_groups) {
@@ -677,6 +727,7 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
         }
     }
     CU(record(db->ev[3], st));
+    if (qp_side) CU(cudaStreamWaitEvent(st, db->join_ev, 0));
     if (P.int16_ok && (P.num_items > 0 || P.mq || P.wave || P.pair)) {
         jp.mode = kIntraRescore;
         CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
@@ -728,7 +779,10 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(score_profile_enabled() ? 1 : 0);
     key.push_back(wave_enabled() ? 1 : 0);
     key.push_back(pair_enabled() ? 1 : 0);
-    key.push_back(forced_pair_blocks_per_sm());
+    {
+        const char* ev = std::getenv("SWGB_LONG_PAIRS");
+        key.push_back(ev ? std::atoll(ev) : -1);
+    }
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
 
@@ -918,10 +972,8 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
     for (int v = 0; v < 3; ++v)
         db->intra_block_occ[v] = block_off ? 0 : intra_block_occupancy(kIntraBlockRows[v], alphabet_size + 1);
-    for (int v = 0; v < 2; ++v) {
-        db->wave_occ[v] = wave_occupancy(kWaveRows[v], alphabet_size + 1);
-        db->wave_ss_occ[v] = wave_ss_occupancy(kWaveSsRows[v], alphabet_size + 1);
-    }
+    for (int v = 0; v < 2; ++v) db->wave_occ[v] = wave_occupancy(kWaveRows[v], alphabet_size + 1);
+    CU(cudaDeviceGetAttribute(&db->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
     const char* forced = std::getenv("SWGB_VARIANT");
@@ -931,6 +983,9 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     }
     CU(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&db->capture_stream, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&db->side_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&db->fork_ev, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&db->join_ev, cudaEventDisableTiming));
     for (auto& e : db->ev) CU(cudaEventCreate(&e));
     const Layout& L = db->layout;
     const size_t inter_bytes = static_cast<size_t>(std::max<int64_t>(L.inter_bytes, 16));
@@ -1010,6 +1065,9 @@ void sw_db_free(sw_db* db) {
             if (e) cudaEventDestroy(e);
         if (db->stream) cudaStreamDestroy(db->stream);
         if (db->capture_stream) cudaStreamDestroy(db->capture_stream);
+        if (db->side_stream) cudaStreamDestroy(db->side_stream);
+        if (db->fork_ev) cudaEventDestroy(db->fork_ev);
+        if (db->join_ev) cudaEventDestroy(db->join_ev);
     }
     delete db;
 }

@@ -101,6 +101,8 @@ struct Plan {
     int pair_rows = 5;
     int pair_grid = 0;
     int64_t g_pair_end = 0;
+    int64_t pair_long_pairs = 0;  // longest slot pairs, run first with one warp per sub-partition
+    int pair_long_blocks = 0;
     WaveParams pair_p{};
     cudaGraphExec_t exec = nullptr;
 };
@@ -138,6 +140,8 @@ struct sw_db {
     swgb::DevBuf<int32_t> h_scores;
     cudaStream_t stream = nullptr;           // stream of the host-buffer API
     cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
+    cudaStream_t side_stream = nullptr;      // a parallel branch of a search (joined by events)
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaEvent_t ev[5] = {};                  // per-kernel timing; ev[4] = end of the last search
     bool done_recorded = false;
     std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 32
@@ -150,7 +154,7 @@ struct sw_db {
     int intra_block_occ[3] = {0, 0, 0};   // 5, 8 and 16 query rows per lane
     int inter_sp_occ = 0;                 // score-profile inter-task kernel
     int wave_occ[2] = {0, 0};             // packed wavefront kernel, 8 and 16 rows per lane
-    int wave_ss_occ[2] = {0, 0};          // its two-subject mode, 5 and 8 rows per lane
+    int max_smem = 0;                     // opt-in shared memory per block (bytes)
     // last search
     sw_stats stats{};
     bool stats_pending = false;

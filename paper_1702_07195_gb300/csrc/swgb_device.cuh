@@ -70,7 +70,8 @@ struct Control {
     unsigned int next_rescore;       // saturation-list counter
     unsigned int flag_count;         // saturated lanes seen by the int16x2 kernels
     unsigned int status;             // bit 0: a query residue code was out of range
-    unsigned int next_wave;          // packed wavefront kernel's block-item counter
+    unsigned int next_wave;          // packed wavefront kernel's item counter
+    unsigned int next_wave_long;     // its queue of the longest slot pairs (two-subject mode)
 };
 
 struct Gaps {
@@ -191,6 +192,12 @@ struct WaveParams {
     const int32_t* group_len;
     const int32_t* perm;
     int64_t group_begin, group_end;
+    int32_t max_group_len;      // two-subject mode: sizes the residue buffers
+    const uint8_t* qres;        // two-subject mode: query residues (query q at qres_off[q]),
+    const int64_t* qres_off;    //   from which the kernel builds its own profile, with
+    const int8_t* matrix;       //   the A x A matrix (device)
+    int64_t long_pairs;         // two-subject mode: the longest slot pairs, served first ...
+    int32_t long_blocks;        // ... by a few warps of blocks [0, long_blocks)
     int32_t alphabet1;
     Control* ctrl;
     FlagEntry* flags;
@@ -206,9 +213,19 @@ size_t wave_smem_bytes(int rows_per_lane, int alphabet1);
 int wave_occupancy(int rows_per_lane, int alphabet1);
 cudaError_t launch_wave_mq(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st);
 constexpr int kWaveSsRows[2] = {5, 8};  // query rows per lane of the two-subject variants
-size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1);
-int wave_ss_occupancy(int rows_per_lane, int alphabet1);
-cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st);
+// Two-subject mode holds the whole query profile in shared memory (one block of
+// wave_ss_warps() warps per SM): wave_ss_fits says whether a query of m rows fits.
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len);
+int wave_ss_warps();
+int wave_ss_blocks_per_sm();
+int wave_ss_long_warps();
+bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem);
+// uint16 entries of a warp's residue buffer: dummy columns, the longest group, and the
+// columns the wavefront's last lanes read past the end, rounded to 16 bytes
+__host__ __device__ constexpr int wave_ss_res_stride(int max_group_len) {
+    return (32 + max_group_len + 64 + 7) / 8 * 8;
+}
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int m, int grid, cudaStream_t st);
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_build_qp(const uint8_t* d_queries, const int64_t* d_qoff, int32_t nq,

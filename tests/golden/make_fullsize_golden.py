@@ -2,7 +2,7 @@
 
     python tests/golden/make_fullsize_golden.py batched [--threads N]
     python tests/golden/make_fullsize_golden.py long_subject [--pairs 2000]
-    python tests/golden/make_fullsize_golden.py paper_shaped [--pairs 600]
+    python tests/golden/make_fullsize_golden.py paper_shaped [--pairs 1200]
 
 Every value comes from ``oracle`` (the int64 CPU recurrence of Eqs. sw2-sw4) on the seeded
 inputs of ``workloads``; nothing here runs or reads the CUDA path.  Run it on the CPU, once.
@@ -14,9 +14,10 @@ each block of ``BLOCK`` consecutive scores (first 16 hex digits), so a test can 
 of a mismatch and recompute only that block.  Rows finished so far are kept in a partial file
 and the run resumes from it.
 
-``long_subject`` and ``paper_shaped`` (1.3e13 and 4.6e13 cells: too many for a full pass)
-store the exact scores of a seeded sample of pairs: the longest subjects against every query,
-then random pairs.
+``long_subject`` (5 queries vs 50,000 subjects of 5,000..35,000 residues) and
+``paper_shaped`` (the 20 queries vs 6M sequences) -- 1.3e13 and 4.6e13 cells, too many for a
+full pass -- store the exact scores of a seeded sample of pairs: the 50 (20) longest subjects
+against every query, then random pairs.
 
 Each file also records fingerprints of the inputs (SHA-256 of the residues, offsets, queries
 and matrix), so a test can tell a changed generator from a wrong score.
@@ -145,8 +146,7 @@ def main():
     elif a.workload == "long_subject":
         print(make_sampled("long_subject", a.pairs or 2000, 50, a.threads))
     else:
-        print(make_sampled("paper_shaped", a.pairs or 600, 20, a.threads,
-                           query_lengths=[144, 807, 5478]))
+        print(make_sampled("paper_shaped", a.pairs or 1200, 20, a.threads))
 
 
 if __name__ == "__main__":

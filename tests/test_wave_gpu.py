@@ -169,14 +169,19 @@ def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, monkeypatch):
 
 @pytest.mark.parametrize("flag_cap", [0, 1])
 def test_two_subject_saturation_rescored(sw, flag_cap, monkeypatch):
+    """Hits above the int16 range in the two-subject mode: a matrix whose W/W entry is 120 lets
+    a 300-residue query (whose profile fits in shared memory) score 36,000 against a run of W;
+    those lanes are flagged and rescored in int32, with and without overflow of the list."""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
     wl = w.plain(seed=41, scale=0.03)
-    db2, q2, idx = w.plant_saturating(wl.db, wl.queries[0][:30], count=5, run=3100)
-    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, long_cutoff=8192,
-                       flag_cap=flag_cap) as h:
-        got = sw.sw_search(h, q2, wl.matrix, 10, 2)
+    sm = wl.matrix.copy()
+    sm[w.CODE_W, w.CODE_W] = 120
+    q = np.concatenate([w.draw_residues(np.random.default_rng(2), 20), np.full(300, w.CODE_W, np.uint8)])
+    db2, _, idx = w.plant_saturating(wl.db, q[:20], count=5, run=300)
+    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, flag_cap=flag_cap) as h:
+        got = sw.sw_search(h, q, sm, 10, 2)
         st = sw.sw_get_stats(h)
-    exp = _oracle([q2], db2, wl.matrix, 10, 2)
+    exp = _oracle([q], db2, sm, 10, 2)
     _check(got[None], exp, f"saturation, flag_cap {flag_cap}")
     assert exp.max() > 32767 and st["flagged"] >= 3 and st["intra_packed"] == 2
 
