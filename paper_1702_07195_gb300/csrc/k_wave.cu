@@ -54,46 +54,46 @@ __device__ __forceinline__ unsigned pack2(int v) {
     return (static_cast<unsigned>(v) & 0xFFFFu) * 0x00010001u;
 }
 
-// One query row of a column step on both halves: Eqs. sw2-sw4 on (H - Goe) state with the
-// biased score S' = SM + Goe (the same update as the inter-task kernels).
-__device__ __forceinline__ unsigned cell2(unsigned& d, unsigned& hm, unsigned& e, unsigned& f,
-                                          unsigned sc, const PackedGaps& k) {
-    const unsigned x = __viaddmax_s16x2_relu(d, sc, e);      // max(0, H_diag + S, E)
-    const unsigned xm = __viaddmax_s16x2(x, k.ngoe, k.floor);  // X - Goe
-    d = hm;
-    hm = __viaddmax_s16x2(f, k.ngoe, xm);                    // H - Goe = max(F, X) - Goe
-    e = __viaddmax_s16x2(e, k.nge, hm);                      // E of the next column
-    f = __viaddmax_s16x2(f, k.ngep, xm);                     // F of the next row
-    return x;
-}
-
-// One column step of a lane's kTB rows on both halves, in two phases: first X (and X - Goe)
-// of every row from the previous column's state -- row r's diagonal is row r - 1's H - Goe
-// of the previous column, still in Hm[r - 1] (d for row 0) -- then the F chain down the rows,
-// which overwrites Hm and E in place.  Same operations as kTB calls of cell2, without the
-// register rotation that keeping the old Hm[r] for the next row needs there.
-template <int kTB>
+// One column step of a lane's kTB rows on both halves.  Rows go in sub-blocks of up to four:
+// first X (and X - Goe) of the sub-block's rows from the previous column's state -- row r's
+// diagonal is row r - 1's H - Goe of the previous column, still in Hm[r - 1] (for the first row
+// of a sub-block it was saved before the previous sub-block overwrote it) -- then the F chain
+// down the sub-block, which overwrites Hm and E in place.  The same operations as a row-by-row
+// update of Eqs. sw2-sw4, without a register rotation per row.
+// `score(rb, sc)` fills sc[0..3] with the packed scores S' of rows rb..rb+3.
+template <int kTB, class ScoreFn>
 __device__ __forceinline__ void column2(unsigned (&Hm)[kTB], unsigned (&E)[kTB], unsigned& F,
-                                        const unsigned d, const unsigned (&sc)[kTB],
-                                        const PackedGaps& k, unsigned& best) {
-    unsigned xm[kTB];
+                                        const unsigned d, ScoreFn score, const PackedGaps& k,
+                                        unsigned& best) {
+    unsigned diag = d;
 #pragma unroll
-    for (int r = 0; r < kTB; r += 2) {
-        const unsigned xa = __viaddmax_s16x2_relu(r == 0 ? d : Hm[r - 1], sc[r], E[r]);
-        xm[r] = __viaddmax_s16x2(xa, k.ngoe, k.floor);
-        if (r + 1 < kTB) {
-            const unsigned xb = __viaddmax_s16x2_relu(Hm[r], sc[r + 1], E[r + 1]);
-            xm[r + 1] = __viaddmax_s16x2(xb, k.ngoe, k.floor);
-            best = __vimax3_s16x2(best, xa, xb);
-        } else {
-            best = __vmaxs2(best, xa);
+    for (int rb = 0; rb < kTB; rb += 4) {
+        constexpr int kSub = 4;
+        unsigned xm[kSub], sc[kSub];
+        score(rb, sc);
+#pragma unroll
+        for (int i = 0; i < kSub; i += 2) {
+            const int r = rb + i;
+            if (r >= kTB) break;
+            const unsigned xa = __viaddmax_s16x2_relu(i == 0 ? diag : Hm[r - 1], sc[i], E[r]);
+            xm[i] = __viaddmax_s16x2(xa, k.ngoe, k.floor);
+            if (r + 1 < kTB) {
+                const unsigned xb = __viaddmax_s16x2_relu(Hm[r], sc[i + 1], E[r + 1]);
+                xm[i + 1] = __viaddmax_s16x2(xb, k.ngoe, k.floor);
+                best = __vimax3_s16x2(best, xa, xb);
+            } else {
+                best = __vmaxs2(best, xa);
+            }
         }
-    }
+        if (rb + kSub < kTB) diag = Hm[rb + kSub - 1];   // old H - Goe: diagonal of the next row
 #pragma unroll
-    for (int r = 0; r < kTB; ++r) {
-        Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm[r]);      // H - Goe = max(F, X) - Goe
-        E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);     // E of the next column
-        F = __viaddmax_s16x2(F, k.ngep, xm[r]);          // F of the next row
+        for (int i = 0; i < kSub; ++i) {
+            const int r = rb + i;
+            if (r >= kTB) break;
+            Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm[i]);   // H - Goe = max(F, X) - Goe
+            E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);  // E of the next column
+            F = __viaddmax_s16x2(F, k.ngep, xm[i]);       // F of the next row
+        }
     }
 }
 
@@ -120,17 +120,19 @@ __device__ __forceinline__ uint2 mask_boundary(uint2 v, unsigned keep, unsigned 
 // takes subjects [i * kWaveBW, (i + 1) * kWaveBW) of the list (longest first), one per warp,
 // and runs every step of the two-stream pass list over them.
 template <int kTB>
-__global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WaveParams p) {
+__global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const WaveParams p) {
     constexpr int kBlock = kWaveBW * kWarp;
     constexpr int kRowsB = kTB * kWarp;
     constexpr int kPStride = slice_stride<kTB>();   // words per residue row of the slice
     static_assert(kTB % 4 == 0, "rows per lane: whole 16-byte profile loads");
     extern __shared__ __align__(16) uint32_t s_pp[];   // (A + 1) x kPStride
     __shared__ int s_item;
+    __shared__ uint8_t s_ring[kWaveBW][256];           // per-warp residue rings
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
     const int my_chunk = chunk_offset<kTB>(lane);
     int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kWaveBW + warp) * p.spill_stride;
+    uint8_t* ring = s_ring[warp];
     PackedGaps k;
     k.ngoe = pack2(-p.gaps.goe);
     k.nge = pack2(-p.gaps.ge);
@@ -187,14 +189,32 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WavePar
                         sp_next = mask_boundary(reinterpret_cast<const uint2*>(spill)[32 + lane],
                                                 keep, init_hm, init_f);
                 }
-                unsigned res_next = lane == 0 ? subj[0] : 0u;
+                // Residue ring of this warp: column c at ring[c & 127] and ring[(c & 127) + 128]
+                // (a mirror, so that a block of 32 steps reads without wrapping); columns
+                // outside [0, n) hold the dummy code.  During the 32-step block starting at tb it
+                // holds [tb - 31, tb + 33); at the block's start the lanes write the columns the
+                // next block adds, loaded from global memory one block ahead.
+                const unsigned dummy = static_cast<unsigned>(p.alphabet1 - 1);
+                auto res_at = [&](const int c) -> unsigned {
+                    return (c >= 0 && c < n) ? static_cast<unsigned>(subj[c]) : dummy;
+                };
+                auto ring_put = [&](const int c, const unsigned v) {
+                    ring[c & 127] = static_cast<uint8_t>(v);
+                    ring[(c & 127) + 128] = static_cast<uint8_t>(v);
+                };
+                ring_put(lane - 32, dummy);
+                ring_put(lane, res_at(lane));
+                if (lane == 0) ring_put(32, res_at(32));
+                unsigned res_ahead = res_at(33 + lane);   // the next block's columns
+                __syncwarp();
+                unsigned res_next = ring[(-lane) & 127];   // column -lane: step 0
                 const int steps = n + kWarp - 1;
-                // Step t: lane l updates column j = t - l.  Lane 0 takes the previous pass's row
-                // of column t from lane (t mod 32) of sp_cur (columns [32 k, 32 k + 32) during
-                // steps [32 k, 32 k + 32)); when both halves start a query (`on_first`) that row
-                // is the zero boundary, a constant.  The residue of the next step's column is
-                // loaded one step ahead.
-                auto step = [&](const int t, const int src, auto checked, auto on_first) {
+                // Step t: lane l updates column j = t - l (every lane, every step: a column outside
+                // the subject is a dummy column, exact as for the two-subject mode).  Lane 0 takes
+                // the previous pass's row of column t from lane (t mod 32) of sp_cur (columns
+                // [32 k, 32 k + 32) during steps [32 k, 32 k + 32)); when both halves start a
+                // query (`on_first`) that row is the zero boundary, a constant.
+                auto step = [&](const int t, const int src, const uint8_t* rnext, auto on_first) {
                     const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                     const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
                     unsigned l0_hm = init_hm, l0_f = init_f;
@@ -202,28 +222,24 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WavePar
                         l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src);
                         l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src);
                     }
-                    const int j = t - lane;
                     const unsigned res = res_next;
-                    if (j + 1 >= 0 && j + 1 < n) res_next = subj[j + 1];
-                    if (decltype(checked)::value && !(j >= 0 && j < n)) return;
+                    res_next = *rnext;                         // column j + 1
                     unsigned F = lane == 0 ? l0_f : up_f;     // F(r0, j)
                     const unsigned d = hm_prev;                // (H - Goe)(r0 - 1, j - 1)
                     hm_prev = lane == 0 ? l0_hm : up_hm;       // (H - Goe)(r0 - 1, j)
                     const uint4* prow = reinterpret_cast<const uint4*>(s_pp + res * kPStride + my_chunk);
-                    unsigned sc[kTB];
-#pragma unroll
-                    for (int r4 = 0; r4 < kTB; r4 += 4) {
-                        const uint4 sv = prow[r4 >> 2];
-                        sc[r4] = sv.x;
-                        sc[r4 + 1] = sv.y;
-                        sc[r4 + 2] = sv.z;
-                        sc[r4 + 3] = sv.w;
-                    }
-                    column2<kTB>(Hm, E, F, d, sc, k, best);
+                    column2<kTB>(Hm, E, F, d, [&](const int rb, unsigned (&sc)[4]) {
+                        const uint4 sv = prow[rb >> 2];
+                        sc[0] = sv.x;
+                        sc[1] = sv.y;
+                        sc[2] = sv.z;
+                        sc[3] = sv.w;
+                    }, k, best);
                     out_hm = Hm[kTB - 1];
                     out_f = F;
-                    if (lane == kWarp - 1 && write) spill[j] = make_int2(static_cast<int>(out_hm),
-                                                                         static_cast<int>(out_f));
+                    const int j = t - lane;
+                    if (write && lane == kWarp - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n))
+                        spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
                 };
                 auto run = [&](auto on_first) {
                     for (int tb = 0; tb < steps; tb += kWarp) {
@@ -236,13 +252,17 @@ __global__ void __launch_bounds__(kWaveBW * kWarp) k_wave_mq_i16x2(const WavePar
                                         keep, init_hm, init_f);
                             }
                         }
-                        if (tb >= kWarp && tb + kWarp <= n) {
-#pragma unroll 1
-                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, std::false_type{}, on_first);
+                        ring_put(tb + 33 + lane, res_ahead);
+                        res_ahead = res_at(tb + 65 + lane);
+                        __syncwarp();
+                        const uint8_t* rbase = ring + ((tb - lane) & 127) + 1;   // column j + 1 at u
+                        if (tb + kWarp <= steps) {
+#pragma unroll 4
+                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first);
                         } else {
-                            const int ue = min(kWarp, steps - tb);
+                            const int ue = steps - tb;
 #pragma unroll 1
-                            for (int u = 0; u < ue; ++u) step(tb + u, u, std::true_type{}, on_first);
+                            for (int u = 0; u < ue; ++u) step(tb + u, u, rbase + u, on_first);
                         }
                     }
                 };
@@ -421,13 +441,16 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 unsigned F = lane == 0 ? l0_f : up_f;
                 const unsigned d = hm_prev;
                 hm_prev = lane == 0 ? l0_hm : up_hm;
-                unsigned sc[kTB];
+                column2<kTB>(Hm, E, F, d, [&](const int rb, unsigned (&sc)[4]) {
 #pragma unroll
-                for (int wi = 0; wi < kW; ++wi) {
-                    sc[2 * wi] = __byte_perm(ca[wi], cb[wi], 0x5410);
-                    if (2 * wi + 1 < kTB) sc[2 * wi + 1] = __byte_perm(ca[wi], cb[wi], 0x7632);
-                }
-                column2<kTB>(Hm, E, F, d, sc, k, best);
+                    for (int i = 0; i < 4; i += 2) {
+                        const int wi = (rb + i) >> 1;
+                        if (wi < kW) {
+                            sc[i] = __byte_perm(ca[wi], cb[wi], 0x5410);
+                            sc[i + 1] = __byte_perm(ca[wi], cb[wi], 0x7632);
+                        }
+                    }
+                }, k, best);
                 out_hm = Hm[kTB - 1];
                 out_f = F;
                 if constexpr (decltype(write)::value) {
@@ -445,8 +468,7 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                         step(t, 0, on_first, write);
                         step(t + 1, 0, on_first, write);
                     }
-                    return;
-                }
+                } else {
                 for (int tb = 0; tb < steps; tb += kWarp) {
                     if constexpr (!decltype(on_first)::value) {
                         if (tb > 0) {
@@ -463,6 +485,7 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
 #pragma unroll 1
                         for (int u = 0; u < ue; ++u) step(tb + u, u, on_first, write);
                     }
+                }
                 }
             };
             const bool last = pass == passes - 1;
