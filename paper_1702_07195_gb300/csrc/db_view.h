@@ -25,6 +25,7 @@ struct DbView {
     const uint8_t* inter;
     const int64_t* group_off;
     const int32_t* group_len;
+    const int32_t* group_cols;
     const int32_t* perm;
     const uint8_t* plain;
     const int64_t* plain_off;

@@ -116,13 +116,21 @@ __device__ __forceinline__ void strip(const uint4* __restrict__ res, int L, uint
         hm_prev = b.z;
         if (!last) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
     };
+    // L (even) columns: whole 8-column chunks, then 1-3 column pairs of the last chunk
     for (int jc = 0; jc < L; jc += 8) {
         const uint4 w = w_next;
         if (jc + 8 < L) w_next = res[((jc >> 3) + 1) * kWarp + lane];
+        if (jc + 8 <= L) {
 #pragma unroll 1
-        for (int q2 = 0; q2 < 2; ++q2) {
-            two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
-            two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
+            for (int q2 = 0; q2 < 2; ++q2) {
+                two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
+                two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
+            }
+        } else {
+            const int np = (L - jc) >> 1;
+            two_columns(w.x, b_a, b_b, jc);
+            if (np > 1) two_columns(w.y, b_b, b_a, jc + 2);
+            if (np > 2) two_columns(w.z, b_a, b_b, jc + 4);
         }
     }
 }
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_i16x2(const In
         const QueryDesc qd = p.queries[item.query];
         const bool active = warp < item.ngroups;
         const int g = item.group + warp;
-        const int L = active ? p.group_len[g] : 0;
+        const int L = active ? p.group_cols[g] : 0;
         const uint4* res =
             active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
         const int S = (qd.m + kT - 1) / kT;

@@ -96,13 +96,22 @@ __device__ __forceinline__ void strip_mq(const uint4* __restrict__ res, int L, i
         hm_prev = b.z;
         if (write) bnd[(j >> 1) * kWarp + lane] = make_uint4(out_hm0, f0, Hm[kT - 1], f1);
     };
+    // L (even) columns: whole 8-column chunks, then 1-3 column pairs of the last chunk (the
+    // storage is padded to 8 columns; the sweep stops at the longest member)
     for (int jc = 0; jc < L; jc += 8) {
         const uint4 w = w_next;
         if (jc + 8 < L) w_next = res[((jc >> 3) + 1) * kWarp + lane];
+        if (jc + 8 <= L) {
 #pragma unroll 1
-        for (int q2 = 0; q2 < 2; ++q2) {
-            two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
-            two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
+            for (int q2 = 0; q2 < 2; ++q2) {
+                two_columns(q2 ? w.z : w.x, b_a, b_b, jc + 4 * q2);
+                two_columns(q2 ? w.w : w.y, b_b, b_a, jc + 4 * q2 + 2);
+            }
+        } else {
+            const int np = (L - jc) >> 1;
+            two_columns(w.x, b_a, b_b, jc);
+            if (np > 1) two_columns(w.y, b_b, b_a, jc + 2);
+            if (np > 2) two_columns(w.z, b_a, b_b, jc + 4);
         }
     }
 }
@@ -155,7 +164,7 @@ __global__ void __launch_bounds__(kW * kWarp, kMinBlocks) k_inter_mq_i16x2(const
         const int s_begin = p.tick ? p.tick->batch_step_off[b] : 0;
         const int s_end = p.tick ? p.tick->batch_step_off[b + 1] : num_steps;
         const int g = hg >> 1, h = hg & 1;
-        const int L = active ? p.group_len[g] : 0;
+        const int L = active ? p.group_cols[g] : 0;
         const uint4* res =
             active ? reinterpret_cast<const uint4*>(p.inter + p.group_off[g]) : nullptr;
         const int id = active ? p.perm[g * kGroupSeqs + 2 * lane + h] : -1;

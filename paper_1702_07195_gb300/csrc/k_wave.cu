@@ -214,7 +214,10 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                 // the previous pass's row of column t from lane (t mod 32) of sp_cur (columns
                 // [32 k, 32 k + 32) during steps [32 k, 32 k + 32)); when both halves start a
                 // query (`on_first`) that row is the zero boundary, a constant.
-                auto step = [&](const int t, const int src, const uint8_t* rnext, auto on_first) {
+                // store: 0 = no pass-boundary row (last step), 1 = lane 31 writes (its column is
+                // inside the subject for the whole block), 2 = lane 31 writes if inside
+                auto step = [&](const int t, const int src, const uint8_t* rnext, auto on_first,
+                                auto store) {
                     const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                     const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
                     unsigned l0_hm = init_hm, l0_f = init_f;
@@ -237,9 +240,14 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                     }, k, best);
                     out_hm = Hm[kTB - 1];
                     out_f = F;
-                    const int j = t - lane;
-                    if (write && lane == kWarp - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n))
-                        spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
+                    if constexpr (decltype(store)::value == 1) {
+                        if (lane == kWarp - 1)
+                            spill[t - lane] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
+                    } else if constexpr (decltype(store)::value == 2) {
+                        const int j = t - lane;
+                        if (lane == kWarp - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n))
+                            spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
+                    }
                 };
                 auto run = [&](auto on_first) {
                     for (int tb = 0; tb < steps; tb += kWarp) {
@@ -256,13 +264,24 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                         res_ahead = res_at(tb + 65 + lane);
                         __syncwarp();
                         const uint8_t* rbase = ring + ((tb - lane) & 127) + 1;   // column j + 1 at u
+                        using NoStore = std::integral_constant<int, 0>;
+                        using Store = std::integral_constant<int, 1>;
+                        using CheckedStore = std::integral_constant<int, 2>;
                         if (tb + kWarp <= steps) {
+                            if (!write) {
 #pragma unroll 4
-                            for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first);
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, NoStore{});
+                            } else if (tb >= kWarp && tb < n) {
+#pragma unroll 4
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, Store{});
+                            } else {
+#pragma unroll 4
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, CheckedStore{});
+                            }
                         } else {
                             const int ue = steps - tb;
 #pragma unroll 1
-                            for (int u = 0; u < ue; ++u) step(tb + u, u, rbase + u, on_first);
+                            for (int u = 0; u < ue; ++u) step(tb + u, u, rbase + u, on_first, CheckedStore{});
                         }
                     }
                 };
@@ -307,8 +326,8 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
 // barrier, so that the wavefronts of the longest subjects, which set the length of a search on
 // a small database, share their SM sub-partitions with fewer warps.  Then every warp serves the
 // rest, longest first.
-constexpr int kSsBW = 8;          // warps per block
-constexpr int kSsBlocksPerSM = 2;
+constexpr int kSsBW = 16;         // warps per block (one block per SM)
+constexpr int kSsBlocksPerSM = 1;
 constexpr int kSsLongWarps = 4;   // warps of a long block that run the first phase
 constexpr int kResPad = 32;       // dummy columns kept before column 0 in a residue buffer
 

@@ -81,6 +81,7 @@ std::string plan_layout(const int64_t* offsets, int64_t num_seqs, int32_t long_c
     out.num_groups = (n_short + kGroup - 1) / kGroup;
     out.group_off.resize(static_cast<size_t>(out.num_groups));
     out.group_len.resize(static_cast<size_t>(out.num_groups));
+    out.group_cols.resize(static_cast<size_t>(out.num_groups));
     out.group_res.assign(static_cast<size_t>(out.num_groups), 0);
     out.perm.assign(static_cast<size_t>(out.num_groups * kGroup), -1);
     int64_t off = 0;
@@ -94,6 +95,7 @@ std::string plan_layout(const int64_t* offsets, int64_t num_seqs, int32_t long_c
             out.short_residues += offsets[id + 1] - offsets[id];
             out.group_res[static_cast<size_t>(g)] += offsets[id + 1] - offsets[id];
         }
+        out.group_cols[static_cast<size_t>(g)] = static_cast<int32_t>((glen + 1) / 2 * 2);
         glen = (glen + 7) / 8 * 8;
         out.group_len[static_cast<size_t>(g)] = static_cast<int32_t>(glen);
         out.group_off[static_cast<size_t>(g)] = off;

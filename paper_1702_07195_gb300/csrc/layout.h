@@ -19,7 +19,8 @@ struct Layout {
     int32_t max_len = 0;         // longest sequence overall
     int64_t short_residues = 0;  // residues covered by the interleaved groups
     std::vector<int64_t> group_off;
-    std::vector<int32_t> group_len;
+    std::vector<int32_t> group_len;   // columns of the group's storage (multiple of 8)
+    std::vector<int32_t> group_cols;  // columns the kernels sweep: longest member, rounded to 2
     std::vector<int64_t> group_res;   // real residues per group
     std::vector<int32_t> perm;      // num_groups * 64, -1 for fillers
     std::vector<int32_t> long_ids;  // longest first

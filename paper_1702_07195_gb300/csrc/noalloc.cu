@@ -251,6 +251,7 @@ extern "C" sw_status sw_search_noalloc(const sw_db* db, const uint8_t* d_query, 
         p.inter = v.inter;
         p.group_off = v.group_off;
         p.group_len = v.group_len;
+        p.group_cols = v.group_cols;
         p.perm = v.perm;
         p.queries = desc;
         p.items = items;

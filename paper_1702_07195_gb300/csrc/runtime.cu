@@ -516,6 +516,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     ip.inter = db->inter_ptr;
     ip.group_off = db->group_off.ptr;
     ip.group_len = db->group_len.ptr;
+    ip.group_cols = db->group_cols.ptr;
     ip.perm = db->perm.ptr;
     ip.queries = P.descs.ptr;
     ip.items = P.items.ptr;
@@ -535,6 +536,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         mp.inter = db->inter_ptr;
         mp.group_off = db->group_off.ptr;
         mp.group_len = db->group_len.ptr;
+        mp.group_cols = db->group_cols.ptr;
         mp.perm = db->perm.ptr;
         mp.queries = P.descs.ptr;
         mp.pp = P.pp.ptr;
@@ -878,6 +880,7 @@ bool db_view(const sw_db* db, DbView* v) {
     v->inter = db->inter_ptr;
     v->group_off = db->group_off.ptr;
     v->group_len = db->group_len.ptr;
+    v->group_cols = db->group_cols.ptr;
     v->perm = db->perm.ptr;
     v->plain = db->plain_ptr;
     v->plain_off = db->plain_off.ptr;
@@ -1005,11 +1008,14 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     }
     CU(db->group_off.ensure(L.group_off.size()));
     CU(db->group_len.ensure(L.group_len.size()));
+    CU(db->group_cols.ensure(L.group_cols.size()));
     CU(db->perm.ensure(L.perm.size()));
     if (!L.group_off.empty()) {
         CU(cudaMemcpy(db->group_off.ptr, L.group_off.data(), sizeof(int64_t) * L.group_off.size(),
                       cudaMemcpyHostToDevice));
         CU(cudaMemcpy(db->group_len.ptr, L.group_len.data(), sizeof(int32_t) * L.group_len.size(),
+                      cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db->group_cols.ptr, L.group_cols.data(), sizeof(int32_t) * L.group_cols.size(),
                       cudaMemcpyHostToDevice));
         CU(cudaMemcpy(db->perm.ptr, L.perm.data(), sizeof(int32_t) * L.perm.size(),
                       cudaMemcpyHostToDevice));
@@ -1053,6 +1059,7 @@ void sw_db_free(sw_db* db) {
         db->h_queries.release();
         db->group_off.release();
         db->group_len.release();
+        db->group_cols.release();
         db->perm.release();
         db->plain_off.release();
         db->long_ids.release();

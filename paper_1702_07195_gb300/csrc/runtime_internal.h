@@ -121,6 +121,7 @@ struct sw_db {
     swgb::DevBuf<uint8_t> inter;
     swgb::DevBuf<int64_t> group_off;
     swgb::DevBuf<int32_t> group_len;
+    swgb::DevBuf<int32_t> group_cols;
     swgb::DevBuf<int32_t> perm;
     swgb::DevBuf<uint8_t> plain;
     swgb::DevBuf<int64_t> plain_off;

@@ -152,6 +152,7 @@ sw_status capture_tick_graphs(sw_server* s, const DbView& v) {
     ip.inter = v.inter;
     ip.group_off = v.group_off;
     ip.group_len = v.group_len;
+    ip.group_cols = v.group_cols;
     ip.perm = v.perm;
     ip.queries = s->descs.ptr;
     ip.items = nullptr;
@@ -170,6 +171,7 @@ sw_status capture_tick_graphs(sw_server* s, const DbView& v) {
     mp.inter = v.inter;
     mp.group_off = v.group_off;
     mp.group_len = v.group_len;
+    mp.group_cols = v.group_cols;
     mp.perm = v.perm;
     mp.queries = s->descs.ptr;
     mp.pp = s->pp.ptr;

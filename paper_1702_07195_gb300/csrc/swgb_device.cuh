@@ -84,6 +84,7 @@ struct InterParams {
     const uint8_t* inter;
     const int64_t* group_off;
     const int32_t* group_len;
+    const int32_t* group_cols;  // columns to sweep per group (longest member, rounded to 2)
     const int32_t* perm;
     const QueryDesc* queries;
     const InterItem* items;
@@ -119,6 +120,7 @@ struct InterMqParams {
     const uint8_t* inter;
     const int64_t* group_off;
     const int32_t* group_len;
+    const int32_t* group_cols;  // columns to sweep per group (longest member, rounded to 2)
     const int32_t* perm;
     const QueryDesc* queries;   // output rows (qp unused)
     const uint32_t* pp;         // paired profile: pp[d * rows_pad + k * T + r] = (S'_a, S'_b)
