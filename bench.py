@@ -380,6 +380,7 @@ def roofline_of(sw, st, workload, sms, f_max, peaks, peak_src, clocks):
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
          "frac": achieved / peak, "traffic": ncu_traffic(workload, kernel, rows),
          "kernel": kernel, "kernel_ms": k_ms, "kernel_cells": int(k_cells),
+         "search_device_ms": st["total_ms"],
          "peak_basis": basis, "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks_source": peak_src}
     if clocks.get("sm_mhz"):
         r["frac_at_observed_clock"] = achieved / (peak * clocks["sm_mhz"] * 1e6 / f_max)

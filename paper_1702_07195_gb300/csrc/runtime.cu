@@ -403,6 +403,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         P.pair_long_pairs = long_pairs;
         P.pair_long_blocks = static_cast<int>(std::min<int64_t>(
             db->sms / 2, (long_pairs + wave_ss_long_warps() - 1) / wave_ss_long_warps()));
+        const char* eb = std::getenv("SWGB_LONG_BLOCKS");
+        if (eb) P.pair_long_blocks = std::max(0, std::min(db->sms, std::atoi(eb)));
     }
 
     // Scratch shared by all plans of this database.
@@ -784,6 +786,8 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     {
         const char* ev = std::getenv("SWGB_LONG_PAIRS");
         key.push_back(ev ? std::atoll(ev) : -1);
+        const char* eb = std::getenv("SWGB_LONG_BLOCKS");
+        key.push_back(eb ? std::atoll(eb) : -1);
     }
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
