@@ -97,6 +97,52 @@ __device__ __forceinline__ void column2(unsigned (&Hm)[kTB], unsigned (&E)[kTB],
     }
 }
 
+// The same column step with the F recurrence of Eq. sw4 unrolled down the lane's rows:
+// F_r = max(F_in - r Ge', Y_r), Y_r = max over i < r of (X_i - Goe - (r - 1 - i) Ge'), Ge' =
+// min(Ge, Goe).  Every F_r is then one operation from the F that arrives from the lane above
+// (instead of r), which shortens the step's dependency chain -- what bounds a wavefront running
+// alone on its SM sub-partition -- at the cost of kTB - 1 more operations per step (the Y
+// chain).  ngep_r[i] holds -(i + 1) Ge' in both halves; the caller checks that
+// Goe + kTB Ge' stays inside the int16 range, so no intermediate wraps.
+template <int kTB, class ScoreFn>
+__device__ __forceinline__ void column2_prefix(unsigned (&Hm)[kTB], unsigned (&E)[kTB], unsigned& F,
+                                               const unsigned d, ScoreFn score,
+                                               const PackedGaps& k, const unsigned (&ngep_r)[kTB],
+                                               unsigned& best) {
+    unsigned xm[kTB];
+#pragma unroll
+    for (int rb = 0; rb < kTB; rb += 4) {
+        unsigned sc[4];
+        score(rb, sc);
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
+            const int r = rb + i;
+            if (r >= kTB) break;
+            const unsigned xa = __viaddmax_s16x2_relu(r == 0 ? d : Hm[r - 1], sc[i], E[r]);
+            xm[r] = __viaddmax_s16x2(xa, k.ngoe, k.floor);
+            if (r + 1 < kTB) {
+                const unsigned xb = __viaddmax_s16x2_relu(Hm[r], sc[i + 1], E[r + 1]);
+                xm[r + 1] = __viaddmax_s16x2(xb, k.ngoe, k.floor);
+                best = __vimax3_s16x2(best, xa, xb);
+            } else {
+                best = __vmaxs2(best, xa);
+            }
+        }
+    }
+    const unsigned f_in = F;
+    unsigned y = xm[0];                                   // Y_1
+    Hm[0] = __viaddmax_s16x2(f_in, k.ngoe, xm[0]);
+    E[0] = __viaddmax_s16x2(E[0], k.nge, Hm[0]);
+#pragma unroll
+    for (int r = 1; r < kTB; ++r) {
+        const unsigned fr = __viaddmax_s16x2(f_in, ngep_r[r - 1], y);   // F_r
+        Hm[r] = __viaddmax_s16x2(fr, k.ngoe, xm[r]);
+        E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);
+        y = __viaddmax_s16x2(y, k.ngep, xm[r]);                          // Y_{r+1}
+    }
+    F = __viaddmax_s16x2(f_in, ngep_r[kTB - 1], y);                     // F of the row below
+}
+
 __device__ __forceinline__ void emit_score(const WaveParams& p, int q, int id, int v) {
     if (id < 0 || q < 0) return;
     int32_t* scores = p.queries[q].scores;
@@ -323,9 +369,10 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
 // Work: the 32 slot pairs of every group in [group_begin, group_end), numbered longest first.
 // The first `long_pairs` of them form a separate queue served in a first phase by the first
 // kSsLongWarps warps of blocks [0, long_blocks) while the block's other warps wait at a
-// barrier, so that the wavefronts of the longest subjects, which set the length of a search on
-// a small database, share their SM sub-partitions with fewer warps.  Then every warp serves the
-// rest, longest first.
+// barrier: the wavefronts of the longest subjects set the length of a search on a small
+// database, and alone on an SM sub-partition their steps run at the latency of the step's
+// dependency chain rather than sharing the sub-partition's issue with other warps.  Then every
+// warp serves the remaining pairs, longest first.
 constexpr int kSsBW = 16;         // warps per block (one block per SM)
 constexpr int kSsBlocksPerSM = 1;
 constexpr int kSsLongWarps = 4;   // warps of a long block that run the first phase
@@ -360,48 +407,60 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
     // The whole query profile (Section 4.3), built here from the query and the matrix:
     // pass, residue d, lane chunk, word w = rows (2w, 2w + 1) of the lane, each S'(q_i, d) =
     // SM(q_i, d) + Goe; the dummy code and rows past the query score 0 (S' = Goe).  A query
-    // residue outside the alphabet sets status bit 0 (reported by the host after the search).
+    // residue outside the alphabet sets status bit 0 (reported by the host after the search)
+    // and scores 0 here.
+    // The matrix goes to shared memory first, so that building a word costs shared-memory reads
+    // only (one query residue pair per thread, then every residue code d).
     const int A = p.alphabet1 - 1;
+    __shared__ int8_t s_mat[kMaxAlphabet * kMaxAlphabet];
+    for (int i = threadIdx.x; i < A * A; i += blockDim.x) s_mat[i] = p.matrix[i];
+    __syncthreads();
     const uint8_t* qres = p.qres + p.qres_off[p.query];
-    auto score = [&](int row, int d) -> int {
-        if (row >= qd.m || d >= A) return bias;
-        const int code = qres[row];
-        if (code >= A) {
-            if (d == 0) atomicOr(&p.ctrl->status, 1u);
-            return bias;
-        }
-        return p.matrix[code * A + d] + bias;
-    };
-    for (int v = threadIdx.x; v < passes * p.alphabet1 * kW * kWarp; v += blockDim.x) {
-        const int ps = v / (p.alphabet1 * kW * kWarp);
-        const int rem0 = v - ps * (p.alphabet1 * kW * kWarp);
-        const int d = rem0 / (kW * kWarp);
-        const int rem = rem0 - d * (kW * kWarp);
+    for (int v = threadIdx.x; v < passes * kW * kWarp; v += blockDim.x) {
+        const int ps = v / (kW * kWarp);                 // pass, lane, word of the lane's rows
+        const int rem = v - ps * (kW * kWarp);
         const int ln = rem / kW, wi = rem - ln * kW;
         const int r0 = ps * kRowsB + ln * kTB + 2 * wi;
-        const int s0 = score(r0, d);
-        const int s1 = 2 * wi + 1 < kTB ? score(r0 + 1, d) : bias;
-        s_sl[ps * slice_words + d * kPStride + chunk_offset<kW>(ln) + wi] =
-            (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
+        const bool has1 = 2 * wi + 1 < kTB;
+        int c0 = r0 < qd.m ? qres[r0] : -1;              // -1: a row past the query
+        int c1 = has1 && r0 + 1 < qd.m ? qres[r0 + 1] : -1;
+        if (c0 >= A || c1 >= A) {
+            atomicOr(&p.ctrl->status, 1u);
+            c0 = c0 >= A ? -1 : c0;
+            c1 = c1 >= A ? -1 : c1;
+        }
+        uint32_t* dst = s_sl + ps * slice_words + chunk_offset<kW>(ln) + wi;
+        for (int d = 0; d < p.alphabet1; ++d) {
+            const int s0 = (c0 >= 0 && d < A) ? s_mat[c0 * A + d] + bias : bias;
+            const int s1 = (c1 >= 0 && d < A) ? s_mat[c1 * A + d] + bias : bias;
+            dst[d * kPStride] = (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
+        }
     }
     __syncthreads();
 
-    // One slot pair (pair index pi, 0 = the longest) over every pass.
-    auto align_pair = [&](const int64_t pi) {
-        const int64_t g = p.group_end - 1 - pi / (kGroupSeqs / 2);
-        const int t = kGroupSeqs / 2 - 1 - static_cast<int>(pi % (kGroupSeqs / 2));
-        const int id_a = p.perm[g * kGroupSeqs + 2 * t];
-        const int id_b = p.perm[g * kGroupSeqs + 2 * t + 1];
-        const int n_a = id_a >= 0 ? static_cast<int>(p.plain_off[id_a + 1] - p.plain_off[id_a]) : 0;
-        const int n_b = id_b >= 0 ? static_cast<int>(p.plain_off[id_b + 1] - p.plain_off[id_b]) : 0;
-        const int n = max(n_a, n_b);
-        // residue pairs of columns [0, n rounded up to 8) from the interleaved group (16 bytes
-        // = 8 columns per load; past each subject's end the layout holds the dummy code), the
-        // dummy pair elsewhere in [-kResPad, n + kWarp + 1)
-        const uint4* src = reinterpret_cast<const uint4*>(p.inter + p.group_off[g] + t * 16);
+    // Slot pair pi (0 = the longest): its group, pair index t, subject ids and lengths.
+    struct PairRef {
+        int64_t g;
+        int t, id[2], n[2];
+    };
+    auto pair_ref = [&](const int64_t pi) {
+        PairRef r;
+        r.g = p.group_end - 1 - pi / (kGroupSeqs / 2);
+        r.t = kGroupSeqs / 2 - 1 - static_cast<int>(pi % (kGroupSeqs / 2));
+        for (int h = 0; h < 2; ++h) {
+            r.id[h] = p.perm[r.g * kGroupSeqs + 2 * r.t + h];
+            r.n[h] = r.id[h] >= 0 ? static_cast<int>(p.plain_off[r.id[h] + 1] - p.plain_off[r.id[h]]) : 0;
+        }
+        return r;
+    };
+    // Residue pairs of columns [0, n rounded up to 8) from the interleaved group (16 bytes = 8
+    // columns per load; past each subject's end the layout holds the dummy code), the dummy pair
+    // elsewhere in [-kResPad, n + kWarp + 1).  Uniform trip counts (predicated bodies): the warp
+    // stays converged.
+    auto stage_residues = [&](const PairRef& r, const int n) {
+        const uint4* src = reinterpret_cast<const uint4*>(p.inter + p.group_off[r.g] + r.t * 16);
         const int chunks = (n + 7) >> 3;
-        __syncwarp();   // the previous pair's steps have read the buffer
-        // uniform trip counts (predicated bodies): the warp stays converged
+        __syncwarp();   // the previous item's steps have read the buffer
         for (int c0 = 0; c0 < chunks; c0 += kWarp) {
             const int c = c0 + lane;
             if (c < chunks)
@@ -411,6 +470,20 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
         for (int c0 = kResPad + 8 * chunks; c0 < kResPad + n + kWarp + 2; c0 += kWarp)
             if (c0 + lane < kResPad + n + kWarp + 2) rbuf[c0 + lane] = dummy2;
         __syncwarp();
+    };
+
+    // -(r + 1) Ge' in both halves, for the unrolled F recurrence of the first phase
+    unsigned ngep_r[kTB];
+#pragma unroll
+    for (int r = 0; r < kTB; ++r) ngep_r[r] = pack2(-(r + 1) * p.gaps.gep);
+
+    // One slot pair (pair index pi, 0 = the longest) over every pass, both subjects packed;
+    // `prefix`: the F recurrence unrolled down the lane's rows (a shorter dependency chain).
+    auto align_pair = [&](const int64_t pi, auto prefix) {
+        const PairRef r = pair_ref(pi);
+        const int id_a = r.id[0], id_b = r.id[1];
+        const int n = max(r.n[0], r.n[1]);
+        stage_residues(r, n);
         const uint16_t* rcol = rbuf + kResPad - lane;   // rcol[t] = residues of column t - lane
         unsigned best = 0;
         for (int pass = 0; n > 0 && pass < passes; ++pass) {
@@ -460,7 +533,7 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 unsigned F = lane == 0 ? l0_f : up_f;
                 const unsigned d = hm_prev;
                 hm_prev = lane == 0 ? l0_hm : up_hm;
-                column2<kTB>(Hm, E, F, d, [&](const int rb, unsigned (&sc)[4]) {
+                auto score = [&](const int rb, unsigned (&sc)[4]) {
 #pragma unroll
                     for (int i = 0; i < 4; i += 2) {
                         const int wi = (rb + i) >> 1;
@@ -469,7 +542,11 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                             sc[i + 1] = __byte_perm(ca[wi], cb[wi], 0x7632);
                         }
                     }
-                }, k, best);
+                };
+                if constexpr (decltype(prefix)::value)
+                    column2_prefix<kTB>(Hm, E, F, d, score, k, ngep_r, best);
+                else
+                    column2<kTB>(Hm, E, F, d, score, k, best);
                 out_hm = Hm[kTB - 1];
                 out_f = F;
                 if constexpr (decltype(write)::value) {
@@ -531,6 +608,7 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
         __syncwarp();
     };
 
+    // First phase: the longest slot pairs, alone on their SM sub-partitions.
     const int64_t long_pairs = min(p.long_pairs, total_pairs);
     if (static_cast<int>(blockIdx.x) < p.long_blocks) {
         if (warp < kSsLongWarps) {
@@ -539,7 +617,10 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 if (lane == 0) it = atomicAdd(&p.ctrl->next_wave_long, 1u);
                 it = __shfl_sync(0xffffffffu, it, 0);
                 if (it >= long_pairs) break;
-                align_pair(it);
+                if (p.prefix_f)
+                    align_pair(it, std::true_type{});
+                else
+                    align_pair(it, std::false_type{});
             }
         }
         __syncthreads();   // the block's other warps wait here: one active warp per sub-partition
@@ -549,7 +630,7 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
         if (lane == 0) it = atomicAdd(&p.ctrl->next_wave, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (long_pairs + it >= total_pairs) break;
-        align_pair(long_pairs + it);
+        align_pair(long_pairs + it, std::false_type{});
     }
 }
 

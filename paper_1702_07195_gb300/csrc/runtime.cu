@@ -589,6 +589,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         wp.group_begin = P.g_split;
         wp.group_end = P.g_pair_end;
         wp.long_pairs = P.pair_long_pairs;
+        wp.prefix_f = static_cast<int64_t>(goe) + static_cast<int64_t>(P.pair_rows) * std::min(goe, ge) <= 32767 ? 1 : 0;
         wp.max_group_len = db->layout.max_group_len;
         wp.qres_off = P.qoff.ptr;
         wp.matrix = P.matrix.ptr;
@@ -733,8 +734,10 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     CU(record(db->ev[3], st));
     if (qp_side) CU(cudaStreamWaitEvent(st, db->join_ev, 0));
     if (P.int16_ok && (P.num_items > 0 || P.mq || P.wave || P.pair)) {
+        // one block per SM: saturated lanes are rare (the list is usually empty, and a launch
+        // of blocks that find it empty costs in proportion to their number)
         jp.mode = kIntraRescore;
-        CU(launch_intra(jp, P.intra_grid, intra_block_threads(), st));
+        CU(launch_intra(jp, std::min(P.intra_grid, db->sms), intra_block_threads(), st));
         ++launches;
     }
     CU(record(db->ev[4], st));

@@ -200,6 +200,7 @@ struct WaveParams {
     const int8_t* matrix;       //   the A x A matrix (device)
     int64_t long_pairs;         // two-subject mode: the longest slot pairs, served first ...
     int32_t long_blocks;        // ... by a few warps of blocks [0, long_blocks)
+    int32_t prefix_f;           // first phase: F recurrence unrolled (Goe + rows x Ge' < 2^15)
     int32_t alphabet1;
     Control* ctrl;
     FlagEntry* flags;

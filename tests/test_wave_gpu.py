@@ -134,11 +134,14 @@ def test_equals_int32_kernels(sw, monkeypatch):
 
 
 # ------------------------------------------------------------------ two-subject mode
+@pytest.mark.parametrize("long_pairs", ["0", "7", "100000"])
 @pytest.mark.parametrize("m", [1, 31, 144, 159, 160, 161, 256, 300, 321, 700])
-def test_two_subject_wavefront_matches_oracle(sw, m, monkeypatch):
+def test_two_subject_wavefront_matches_oracle(sw, m, long_pairs, monkeypatch):
     """One query against a small database whose groups are all routed off the inter-task
-    kernel: the two subjects of each slot pair share a warp (passes of 160 or 256 rows)."""
+    kernel: the two subjects of each slot pair share a warp (passes of 160 or 256 rows); the
+    longest pairs' subjects run first, one per warp in int32 (none, seven pairs, or all)."""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
+    monkeypatch.setenv("SWGB_LONG_PAIRS", long_pairs)
     rng = np.random.default_rng(1000 + m)
     lens = np.concatenate([rng.integers(0, 500, size=200), [0, 1, 31, 32, 33, 1200], rng.integers(0, 9, size=7)])
     db = w.database_from_lengths(rng, lens)          # 213 sequences: the last group has fillers
@@ -151,9 +154,13 @@ def test_two_subject_wavefront_matches_oracle(sw, m, monkeypatch):
     assert st["intra_packed"] == 2 and st["inter_cells"] == 0
 
 
-@pytest.mark.parametrize("goe,ge", [(0, 0), (2, 9), (12, 2), (16383, 1)])
-def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, monkeypatch):
+@pytest.mark.parametrize("long_pairs", ["0", "100000"])
+@pytest.mark.parametrize("goe,ge", [(0, 0), (2, 9), (12, 2), (16383, 1), (16383, 16383)])
+def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, long_pairs, monkeypatch):
+    """Gap regimes (the first phase unrolls the F recurrence when Goe + rows x min(Ge, Goe)
+    fits int16, and keeps the row-by-row chain otherwise), asymmetric matrix, 7 letters."""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
+    monkeypatch.setenv("SWGB_LONG_PAIRS", long_pairs)
     rng = np.random.default_rng(7 * goe + ge)
     A = 7
     sm = rng.integers(-5, 9, size=(A, A)).astype(np.int8)     # asymmetric
@@ -171,8 +178,10 @@ def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, monkeypatch):
 def test_two_subject_saturation_rescored(sw, flag_cap, monkeypatch):
     """Hits above the int16 range in the two-subject mode: a matrix whose W/W entry is 120 lets
     a 300-residue query (whose profile fits in shared memory) score 36,000 against a run of W;
-    those lanes are flagged and rescored in int32, with and without overflow of the list."""
+    those lanes are flagged and rescored in int32, with and without overflow of the list.  (No
+    first phase: the planted subjects are among the longest, which it would align in int32.)"""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
+    monkeypatch.setenv("SWGB_LONG_PAIRS", "0")
     wl = w.plain(seed=41, scale=0.03)
     sm = wl.matrix.copy()
     sm[w.CODE_W, w.CODE_W] = 120
