@@ -388,11 +388,14 @@ def roofline_of(sw, st, workload, sms, f_max, peaks, peak_src, clocks):
 
 
 def dtype_of(st):
+    """Arithmetic of the search: int16x2 lanes (exact int32 rescore of saturated lanes) on the
+    inter-task kernels and the packed wavefront kernels, int32 on the other intra-task work."""
     inter_cells, cells = st["inter_cells"], st["cells"]
+    packed_intra = bool(st.get("intra_packed"))
+    if inter_cells == cells or (inter_cells == 0 and packed_intra) or packed_intra:
+        return "int16x2 (int32 rescore)"
     if inter_cells == 0:
         return "int32"
-    if inter_cells == cells:
-        return "int16x2 (int32 rescore)"
     return (f"int16x2 (int32 rescore) for {inter_cells / max(1, cells):.1%} of cells, "
             "int32 for the rest")
 
