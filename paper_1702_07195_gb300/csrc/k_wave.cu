@@ -640,8 +640,9 @@ const void* wave_ss_fn(int rows_per_lane) {
 }
 
 const void* wave_mq_fn(int rows_per_lane) {
-    return rows_per_lane == 8 ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<8>)
-                              : reinterpret_cast<const void*>(&k_wave_mq_i16x2<16>);
+    return rows_per_lane == 8    ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<8>)
+           : rows_per_lane == 12 ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<12>)
+                                 : reinterpret_cast<const void*>(&k_wave_mq_i16x2<16>);
 }
 
 }  // namespace
@@ -649,7 +650,9 @@ const void* wave_mq_fn(int rows_per_lane) {
 int wave_warps() { return kWaveBW; }
 
 size_t wave_smem_bytes(int rows_per_lane, int alphabet1) {
-    const int stride = rows_per_lane == 8 ? slice_stride<8>() : slice_stride<16>();
+    const int stride = rows_per_lane == 8    ? slice_stride<8>()
+                       : rows_per_lane == 12 ? slice_stride<12>()
+                                             : slice_stride<16>();
     return static_cast<size_t>(alphabet1) * stride * sizeof(uint32_t);
 }
 
@@ -708,6 +711,8 @@ cudaError_t launch_wave_mq(const WaveParams& p, int rows_per_lane, int grid, cud
     if (e != cudaSuccess) return e;
     if (rows_per_lane == 8)
         k_wave_mq_i16x2<8><<<grid, kWaveBW * kWarp, smem, st>>>(p);
+    else if (rows_per_lane == 12)
+        k_wave_mq_i16x2<12><<<grid, kWaveBW * kWarp, smem, st>>>(p);
     else
         k_wave_mq_i16x2<16><<<grid, kWaveBW * kWarp, smem, st>>>(p);
     return cudaGetLastError();

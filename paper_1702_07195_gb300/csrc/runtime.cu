@@ -266,24 +266,27 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     // with fewer padded rows, charging about 10 operations of per-step overhead per lane).
     std::vector<MqStep> wsteps;
     P.wave = wave_enabled() && P.int16_ok && nonempty >= 2 && !db->layout.long_ids.empty() &&
-             db->wave_occ[0] > 0 && db->wave_occ[1] > 0;
+             db->wave_occ[0] > 0 && db->wave_occ[1] > 0 && db->wave_occ[2] > 0;
     if (P.wave) {
+        // the pass height with the fewest computed rows (both streams, padding included),
+        // charging about 10 operations of per-step overhead per lane
         double best_cost = 1e300;
-        for (int v = 0; v < 2; ++v) {
-            const double rows = 32.0 * kWaveRows[v];
-            double cost = 0.0;
-            for (int q = 0; q < nq; ++q)
-                cost += std::ceil(P.m[static_cast<size_t>(q)] / rows) * rows * (5.5 + 10.0 / kWaveRows[v]);
+        for (int v = 0; v < 3; ++v) {
+            const int T = 32 * kWaveRows[v];
+            const double steps_v = static_cast<double>(build_streams(P.m, order, T).size());
+            const double cost = steps_v * 2.0 * T * (5.5 + 10.0 / kWaveRows[v]);
             if (cost < best_cost * 0.999) {
                 best_cost = cost;
                 P.wave_rows = kWaveRows[v];
             }
         }
+        const char* wr = std::getenv("SWGB_WAVE_ROWS");
+        if (wr && (std::atoi(wr) == 8 || std::atoi(wr) == 12 || std::atoi(wr) == 16)) P.wave_rows = std::atoi(wr);
         const int T = 32 * P.wave_rows;
         wsteps = build_streams(P.m, order, T);
         P.num_wsteps = static_cast<int32_t>(wsteps.size());
         P.wrows_pad = round_up(static_cast<int64_t>(P.num_wsteps) * T, kQpRows);
-        const int occ = db->wave_occ[P.wave_rows == 8 ? 0 : 1];
+        const int occ = db->wave_occ[P.wave_rows == 8 ? 0 : P.wave_rows == 12 ? 1 : 2];
         const int64_t items = (static_cast<int64_t>(db->layout.long_ids.size()) + wave_warps() - 1) / wave_warps();
         P.wave_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(items, static_cast<int64_t>(db->sms) * occ)));
     }
@@ -791,6 +794,8 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
         key.push_back(ev ? std::atoll(ev) : -1);
         const char* eb = std::getenv("SWGB_LONG_BLOCKS");
         key.push_back(eb ? std::atoll(eb) : -1);
+        const char* wr = std::getenv("SWGB_WAVE_ROWS");
+        key.push_back(wr ? std::atoll(wr) : -1);
     }
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
@@ -982,7 +987,7 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     const bool block_off = std::getenv("SWGB_INTRA_BLOCK") && std::getenv("SWGB_INTRA_BLOCK")[0] == '0';
     for (int v = 0; v < 3; ++v)
         db->intra_block_occ[v] = block_off ? 0 : intra_block_occupancy(kIntraBlockRows[v], alphabet_size + 1);
-    for (int v = 0; v < 2; ++v) db->wave_occ[v] = wave_occupancy(kWaveRows[v], alphabet_size + 1);
+    for (int v = 0; v < 3; ++v) db->wave_occ[v] = wave_occupancy(kWaveRows[v], alphabet_size + 1);
     CU(cudaDeviceGetAttribute(&db->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (db->inter_occ[0] <= 0 || db->intra_occ <= 0)
         return fail(SW_ERR_CUDA, "kernels cannot be resident on device %d", dev);
@@ -1125,20 +1130,29 @@ sw_status sw_search_batch(const sw_db* cdb, const uint8_t* const* queries,
         if (query_lens[q] > 0 && !queries[q]) return fail(SW_ERR_ARG, "query %d is null", q);
         qoff[static_cast<size_t>(q) + 1] = qoff[static_cast<size_t>(q)] + query_lens[q];
     }
-    std::vector<uint8_t> cat(static_cast<size_t>(std::max<int64_t>(qoff.back(), 1)));
+    const size_t qbytes = static_cast<size_t>(std::max<int64_t>(qoff.back(), 1));
+    if (db->done_recorded) CU(cudaEventSynchronize(db->ev[4]));   // staging buffers may move
+    // the queries are concatenated into pinned host memory (an asynchronous copy; a pageable
+    // source would be staged by the driver), checked, then copied to the device
+    if (db->pinned_q_cap < qbytes) {
+        if (db->pinned_q) cudaFreeHost(db->pinned_q);
+        db->pinned_q = nullptr;
+        db->pinned_q_cap = 0;
+        CU(cudaHostAlloc(reinterpret_cast<void**>(&db->pinned_q), qbytes, cudaHostAllocDefault));
+        db->pinned_q_cap = qbytes;
+    }
+    uint8_t* cat = db->pinned_q;
     for (int q = 0; q < num_queries; ++q)
         if (query_lens[q] > 0)
-            std::memcpy(cat.data() + qoff[static_cast<size_t>(q)], queries[q],
-                        static_cast<size_t>(query_lens[q]));
+            std::memcpy(cat + qoff[static_cast<size_t>(q)], queries[q], static_cast<size_t>(query_lens[q]));
     for (int64_t i = 0; i < qoff.back(); ++i)
-        if (cat[static_cast<size_t>(i)] >= db->A)
+        if (cat[i] >= db->A)
             return fail(SW_ERR_CODE, "query residue %lld has code %d >= alphabet_size %d",
-                        static_cast<long long>(i), cat[static_cast<size_t>(i)], db->A);
+                        static_cast<long long>(i), cat[i], db->A);
     if (num_queries == 0 || N == 0) return SW_OK;
-    if (db->done_recorded) CU(cudaEventSynchronize(db->ev[4]));   // staging buffers may move
-    CU(db->h_queries.ensure(cat.size()));
+    CU(db->h_queries.ensure(qbytes));
     CU(db->h_scores.ensure(static_cast<size_t>(N * num_queries)));
-    CU(cudaMemcpyAsync(db->h_queries.ptr, cat.data(), cat.size(), cudaMemcpyHostToDevice, db->stream));
+    CU(cudaMemcpyAsync(db->h_queries.ptr, cat, qbytes, cudaMemcpyHostToDevice, db->stream));
     sw_status s = search_device(db, db->h_queries.ptr, qoff.data(), num_queries, matrix, gap_open,
                                 gap_extend, db->h_scores.ptr, db->stream);
     if (s != SW_OK) return s;

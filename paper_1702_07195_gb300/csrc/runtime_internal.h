@@ -139,6 +139,8 @@ struct sw_db {
     // host-buffer API staging
     swgb::DevBuf<uint8_t> h_queries;
     swgb::DevBuf<int32_t> h_scores;
+    uint8_t* pinned_q = nullptr;     // pinned host staging of the queries (grown on demand)
+    size_t pinned_q_cap = 0;
     cudaStream_t stream = nullptr;           // stream of the host-buffer API
     cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
     cudaStream_t side_stream = nullptr;      // a parallel branch of a search (joined by events)
@@ -154,7 +156,7 @@ struct sw_db {
     int intra_occ = 0;
     int intra_block_occ[3] = {0, 0, 0};   // 5, 8 and 16 query rows per lane
     int inter_sp_occ = 0;                 // score-profile inter-task kernel
-    int wave_occ[2] = {0, 0};             // packed wavefront kernel, 8 and 16 rows per lane
+    int wave_occ[3] = {0, 0, 0};          // packed wavefront kernel, 8, 12 and 16 rows per lane
     int max_smem = 0;                     // opt-in shared memory per block (bytes)
     // last search
     sw_stats stats{};
@@ -163,5 +165,6 @@ struct sw_db {
     ~sw_db() {
         if (host_inter) cudaFreeHost(host_inter);
         if (host_plain) cudaFreeHost(host_plain);
+        if (pinned_q) cudaFreeHost(pinned_q);
     }
 };

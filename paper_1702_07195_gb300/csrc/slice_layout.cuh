@@ -19,10 +19,12 @@ namespace swgb {
 // w = kTB / 4 bank groups (16 bytes each) wide and packed in w segments of 32 / w chunks, each
 // segment one group further along than a packed layout would put it; the lane -> (segment,
 // chunk) map gives the 8 lanes of a quarter-warp 8 distinct starting groups modulo 8.
-// kTB: 3, 4, 5, 8 or 16 (an odd count, or a multiple of 4 that divides 32).
+// kTB: an odd count (4-byte loads), a multiple of 4 with an odd number of 16-byte groups
+// (12: lane l at group 3 l, and 3 l mod 8 is a permutation of a quarter-warp's groups), or 8 or
+// 16 (the segment layout below).
 template <int kTB>
 __host__ __device__ constexpr int chunk_offset(int lane) {
-    if constexpr (kTB % 2 == 1) {
+    if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1)) {
         return kTB * lane;
     } else {
         constexpr int w = kTB / 4;
@@ -36,7 +38,7 @@ __host__ __device__ constexpr int chunk_offset(int lane) {
 // Words per residue row of the slice: the span of the chunks rounded up to 32 words.
 template <int kTB>
 __host__ __device__ constexpr int slice_stride() {
-    if constexpr (kTB % 2 == 1)
+    if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1))
         return (kTB * kWarp + 31) / 32 * 32;
     else
         return (4 * (33 * (kTB / 4) - 1) + 31) / 32 * 32;
@@ -71,7 +73,7 @@ constexpr bool chunks_conflict_free() {
     return ok;
 }
 static_assert(chunks_conflict_free<3>() && chunks_conflict_free<4>() && chunks_conflict_free<5>() &&
-                  chunks_conflict_free<8>() && chunks_conflict_free<16>(),
+                  chunks_conflict_free<8>() && chunks_conflict_free<12>() && chunks_conflict_free<16>(),
               "profile slice layout");
 
 }  // namespace swgb

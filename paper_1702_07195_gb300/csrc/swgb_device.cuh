@@ -210,7 +210,7 @@ struct WaveParams {
     int64_t spill_stride;
     Gaps gaps;
 };
-constexpr int kWaveRows[2] = {8, 16};   // query rows per lane of the two-query variants
+constexpr int kWaveRows[3] = {8, 12, 16};   // query rows per lane of the two-query variants
 int wave_warps();
 size_t wave_smem_bytes(int rows_per_lane, int alphabet1);
 int wave_occupancy(int rows_per_lane, int alphabet1);

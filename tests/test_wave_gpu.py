@@ -54,7 +54,10 @@ def _db(rng, n_short=60, long_lens=(33, 63, 64, 65, 95, 96, 97, 200, 511, 1000, 
     [1024, 700, 512, 511, 300, 90],   # 16 rows per lane, several queries per stream
     [3000, 40],                       # one long stream against a short one
 ])
-def test_two_query_wavefront_matches_oracle(sw, qlens):
+@pytest.mark.parametrize("rows", ["8", "12", "16"])
+def test_two_query_wavefront_matches_oracle(sw, qlens, rows, monkeypatch):
+    """Every pass height (256, 384 and 512 rows)."""
+    monkeypatch.setenv("SWGB_WAVE_ROWS", rows)
     rng = np.random.default_rng(sum(qlens))
     db = _db(rng)
     qs = [w.draw_residues(rng, n) for n in qlens]
