@@ -9,13 +9,14 @@
 //
 //  two-query mode (k_wave_mq_i16x2): a warp aligns ONE subject against two streams of query
 //  passes, pass k of stream a in the low halves and pass k of stream b in the high halves of
-//  its registers (the pairing of the multi-query inter-task kernel, MqStep lists with
-//  32 x kTB rows per step).  Both halves read the same subject residue, so one 16-byte load of
-//  the paired profile pp[d][row] = (S'_a, S'_b) gives four packed score pairs: 5.5 DPX
-//  operations per cell pair, the inter-task kernels' minimum.  At the first pass of a query
-//  in one half, that half starts from the zero boundary (its lane-0 input is masked to the
-//  initial values); at its last pass the half's running best is reduced over the warp and
-//  emitted.
+//  its registers.  A stream chains its queries at lane granularity (a query of m rows takes
+//  ceil(m / kTB) lanes, WavePass), so a pass wastes rows only at the end of each query's last
+//  lane.  Both halves read the same subject residue, so one 16-byte load of the paired profile
+//  pp[d][row] = (S'_a, S'_b) gives four packed score pairs: 5.5 DPX operations per cell pair,
+//  the inter-task kernels' minimum.  A lane that holds row 0 of a query takes the zero
+//  boundary as its row above (instead of the lane above, or the previous pass); after each
+//  pass the lanes' bests are reduced per query and merged with the query's earlier passes,
+//  and a query's score is emitted after the pass of its last row.
 //
 //  two-subject mode (k_wave_ss_i16x2): a search with one query; a warp aligns the query
 //  against the two subjects in slots 2t and 2t + 1 of an interleaved 64-sequence group, one in
@@ -164,7 +165,7 @@ __device__ __forceinline__ uint2 mask_boundary(uint2 v, unsigned keep, unsigned 
 
 // kTB query rows per lane (passes of 32 * kTB rows), kWaveBW warps per block: block item i
 // takes subjects [i * kWaveBW, (i + 1) * kWaveBW) of the list (longest first), one per warp,
-// and runs every step of the two-stream pass list over them.
+// and runs every pass of the two-stream pass list over them.
 template <int kTB>
 __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const WaveParams p) {
     constexpr int kBlock = kWaveBW * kWarp;
@@ -174,6 +175,9 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
     extern __shared__ __align__(16) uint32_t s_pp[];   // (A + 1) x kPStride
     __shared__ int s_item;
     __shared__ uint8_t s_ring[kWaveBW][256];           // per-warp residue rings
+    __shared__ unsigned s_best[kWaveBW][kWarp];        // per-lane bests of a pass
+    __shared__ int s_carry[kWaveBW][2];                // best so far of the query continuing
+                                                       // into the next pass, per half
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
     const int my_chunk = chunk_offset<kTB>(lane);
@@ -201,8 +205,7 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
             n = static_cast<int>(p.plain_off[seq + 1] - off);
             subj = p.plain + off;
         }
-        unsigned best = 0;
-        for (int ks = 0; ks < p.num_steps; ++ks) {
+        for (int ks = 0; ks < p.num_passes; ++ks) {
             __syncthreads();   // everyone is done with the previous slice
             const int64_t row0 = static_cast<int64_t>(ks) * kRowsB;
             for (int v = threadIdx.x; v < p.alphabet1 * kRowsB; v += kBlock) {
@@ -212,11 +215,16 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                     p.pp[static_cast<int64_t>(d) * p.rows_pad + row0 + r];
             }
             __syncthreads();
-            const MqStep st = p.steps[ks];
-            // halves that start a query here begin at the zero boundary
-            const unsigned keep = ((st.flags & kMqFirstA) ? 0u : 0x0000FFFFu) |
-                                  ((st.flags & kMqFirstB) ? 0u : 0xFFFF0000u);
-            const bool write = ks + 1 < p.num_steps;
+            const WavePass& wpass = p.passes[ks];
+            const uint32_t first_a = wpass.first[0], first_b = wpass.first[1];
+            // a half whose lane 0 starts a query takes the zero boundary instead of the previous
+            // pass's row; lanes past 0 that start a query (`inner`) mask the lane above's row
+            const unsigned keep = ((first_a & 1u) ? 0u : 0x0000FFFFu) | ((first_b & 1u) ? 0u : 0xFFFF0000u);
+            const unsigned my_keep = (((first_a >> lane) & 1u) ? 0u : 0x0000FFFFu) |
+                                     (((first_b >> lane) & 1u) ? 0u : 0xFFFF0000u);
+            const bool inner_starts = ((first_a | first_b) & ~1u) != 0u;
+            const bool write = ks + 1 < p.num_passes;
+            unsigned best = 0;
             if (n > 0) {
                 unsigned Hm[kTB], E[kTB];
 #pragma unroll
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                 // store: 0 = no pass-boundary row (last step), 1 = lane 31 writes (its column is
                 // inside the subject for the whole block), 2 = lane 31 writes if inside
                 auto step = [&](const int t, const int src, const uint8_t* rnext, auto on_first,
-                                auto store) {
+                                auto inner, auto store) {
                     const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
                     const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
                     unsigned l0_hm = init_hm, l0_f = init_f;
@@ -276,6 +284,10 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                     unsigned F = lane == 0 ? l0_f : up_f;     // F(r0, j)
                     const unsigned d = hm_prev;                // (H - Goe)(r0 - 1, j - 1)
                     hm_prev = lane == 0 ? l0_hm : up_hm;       // (H - Goe)(r0 - 1, j)
+                    if constexpr (decltype(inner)::value) {   // row 0 of a query: zero boundary
+                        F = (F & my_keep) | (init_f & ~my_keep);
+                        hm_prev = (hm_prev & my_keep) | (init_hm & ~my_keep);
+                    }
                     const uint4* prow = reinterpret_cast<const uint4*>(s_pp + res * kPStride + my_chunk);
                     column2<kTB>(Hm, E, F, d, [&](const int rb, unsigned (&sc)[4]) {
                         const uint4 sv = prow[rb >> 2];
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                             spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
                     }
                 };
-                auto run = [&](auto on_first) {
+                auto run = [&](auto on_first, auto inner) {
                     for (int tb = 0; tb < steps; tb += kWarp) {
                         if constexpr (!decltype(on_first)::value) {
                             if (tb > 0) {
@@ -316,39 +328,59 @@ __global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const Wave
                         if (tb + kWarp <= steps) {
                             if (!write) {
 #pragma unroll 4
-                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, NoStore{});
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, inner, NoStore{});
                             } else if (tb >= kWarp && tb < n) {
 #pragma unroll 4
-                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, Store{});
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, inner, Store{});
                             } else {
 #pragma unroll 4
-                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, CheckedStore{});
+                                for (int u = 0; u < kWarp; ++u) step(tb + u, u, rbase + u, on_first, inner, CheckedStore{});
                             }
                         } else {
                             const int ue = steps - tb;
 #pragma unroll 1
-                            for (int u = 0; u < ue; ++u) step(tb + u, u, rbase + u, on_first, CheckedStore{});
+                            for (int u = 0; u < ue; ++u) step(tb + u, u, rbase + u, on_first, inner, CheckedStore{});
                         }
                     }
                 };
-                if (keep == 0u)
-                    run(std::true_type{});
-                else
-                    run(std::false_type{});
+                if (keep == 0u) {
+                    if (inner_starts)
+                        run(std::true_type{}, std::true_type{});
+                    else
+                        run(std::true_type{}, std::false_type{});
+                } else {
+                    if (inner_starts)
+                        run(std::false_type{}, std::true_type{});
+                    else
+                        run(std::false_type{}, std::false_type{});
+                }
                 __syncwarp();   // lane 31's spill writes are visible to the next pass
             }
-            const bool last_a = st.flags & kMqLastA, last_b = st.flags & kMqLastB;
-            if (last_a || last_b) {
-                unsigned b = best;
+            // Per half, the lanes of one query are contiguous: the first of them reduces their
+            // bests (and, for a query that began in an earlier pass, the carried best) and
+            // emits the score if the query ends in this pass, else carries it to the next.
+            s_best[warp][lane] = best;
+            __syncwarp();
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) b = __vmaxs2(b, __shfl_xor_sync(0xffffffffu, b, o));
-                if (lane == 0 && seq >= 0) {
-                    if (last_a) emit_score(p, st.qa, seq, static_cast<int>(static_cast<short>(b & 0xFFFFu)));
-                    if (last_b) emit_score(p, st.qb, seq, static_cast<int>(static_cast<short>(b >> 16)));
+            for (int h = 0; h < 2; ++h) {
+                const int q = wpass.q[h][lane];
+                const bool head = q >= 0 && (lane == 0 || wpass.q[h][lane - 1] != q);
+                if (head) {
+                    const uint32_t fbits = h == 0 ? first_a : first_b;
+                    int v = (lane == 0 && !(fbits & 1u)) ? s_carry[warp][h] : 0;
+                    int l2 = lane;
+                    for (; l2 < kWarp && wpass.q[h][l2] == q; ++l2) {
+                        const unsigned w = s_best[warp][l2];
+                        v = max(v, static_cast<int>(static_cast<short>(h == 0 ? (w & 0xFFFFu) : (w >> 16))));
+                    }
+                    if ((wpass.last[h] >> (l2 - 1)) & 1u) {
+                        if (seq >= 0) emit_score(p, q, seq, v);
+                    } else {
+                        s_carry[warp][h] = v;
+                    }
                 }
-                if (last_a) best &= 0xFFFF0000u;
-                if (last_b) best &= 0x0000FFFFu;
             }
+            __syncwarp();
         }
     }
 }
@@ -639,6 +671,41 @@ const void* wave_ss_fn(int rows_per_lane) {
                               : reinterpret_cast<const void*>(&k_wave_ss_i16x2<8>);
 }
 
+// Paired profile of the two-query wavefront: for lane l of pass k,
+// pp[d * rows_pad + k * 32 kTB + l * kTB + r] = (S'(q_a, row0_a + r, d), S'(q_b, row0_b + r, d))
+// with S' = SM + bias, and 0 + bias for the dummy code, rows past a query's end and lanes
+// without a query.
+__global__ void k_build_pp_wave(const uint8_t* __restrict__ queries, const int64_t* __restrict__ qoff,
+                                const WavePass* __restrict__ passes, int32_t num_passes, int32_t kTB,
+                                const int8_t* __restrict__ matrix, int32_t A, int32_t bias,
+                                uint32_t* __restrict__ pp, int64_t rows_pad, Control* ctrl) {
+    const int d = blockIdx.y;
+    const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (row >= rows_pad) return;
+    const int T = kWarp * kTB;
+    const int64_t k = row / T;
+    const int within = static_cast<int>(row - k * T);
+    const int l = within / kTB;
+    const int r = within - l * kTB;
+    int out[2] = {0, 0};
+    if (k < num_passes && d < A) {
+        for (int h = 0; h < 2; ++h) {
+            const int q = passes[k].q[h][l];
+            if (q < 0) continue;
+            const int64_t q0 = qoff[q];
+            const int64_t i = static_cast<int64_t>(passes[k].row0[h][l]) + r;
+            if (i >= qoff[q + 1] - q0) continue;
+            const int code = queries[q0 + i];
+            if (code < A)
+                out[h] = matrix[code * A + d];
+            else
+                atomicOr(&ctrl->status, 1u);
+        }
+    }
+    pp[static_cast<int64_t>(d) * rows_pad + row] =
+        (static_cast<unsigned>(out[0] + bias) & 0xFFFFu) | (static_cast<unsigned>(out[1] + bias) << 16);
+}
+
 const void* wave_mq_fn(int rows_per_lane) {
     return rows_per_lane == 8    ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<8>)
            : rows_per_lane == 12 ? reinterpret_cast<const void*>(&k_wave_mq_i16x2<12>)
@@ -700,6 +767,17 @@ cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int m, int gr
         k_wave_ss_i16x2<5><<<grid, kSsBW * kWarp, smem, st>>>(p);
     else
         k_wave_ss_i16x2<8><<<grid, kSsBW * kWarp, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_pp_wave(const uint8_t* d_queries, const int64_t* d_qoff,
+                                 const WavePass* d_passes, int32_t num_passes, int32_t rows_per_lane,
+                                 const int8_t* d_matrix, int32_t A, int32_t bias, uint32_t* d_pp,
+                                 int64_t rows_pad, Control* ctrl, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(static_cast<unsigned>((rows_pad + threads - 1) / threads), static_cast<unsigned>(A + 1));
+    k_build_pp_wave<<<grid, threads, 0, st>>>(d_queries, d_qoff, d_passes, num_passes, rows_per_lane,
+                                              d_matrix, A, bias, d_pp, rows_pad, ctrl);
     return cudaGetLastError();
 }
 

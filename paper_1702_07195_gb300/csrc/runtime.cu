@@ -157,6 +157,52 @@ std::vector<MqStep> build_streams(const std::vector<int32_t>& m, const std::vect
     return steps;
 }
 
+// Two streams of lanes for the two-query wavefront: a query of m rows takes ceil(m / kTB)
+// lanes; queries (longest first) go to the stream with fewer lanes, and each stream is cut into
+// passes of 32 lanes, so a pass can hold the end of one query and the start of the next.
+std::vector<WavePass> build_wave_passes(const std::vector<int32_t>& m, const std::vector<int32_t>& order,
+                                        int kTB) {
+    std::vector<int32_t> stream[2];
+    int64_t lanes[2] = {0, 0};
+    for (int32_t q : order) {
+        const int32_t mq = m[static_cast<size_t>(q)];
+        if (mq == 0) continue;
+        const int x = lanes[0] <= lanes[1] ? 0 : 1;
+        stream[x].push_back(q);
+        lanes[x] += (mq + kTB - 1) / kTB;
+    }
+    const int64_t num_passes = (std::max(lanes[0], lanes[1]) + kWarp - 1) / kWarp;
+    WavePass none{};
+    for (int x = 0; x < 2; ++x) {
+        none.first[x] = 0xFFFFFFFFu;
+        none.last[x] = 0u;
+        for (int l = 0; l < kWarp; ++l) {
+            none.q[x][l] = -1;
+            none.row0[x][l] = 0;
+        }
+    }
+    std::vector<WavePass> passes(static_cast<size_t>(num_passes), none);
+    for (int x = 0; x < 2; ++x) {
+        int64_t g = 0;
+        for (int32_t q : stream[x]) {
+            const int32_t L = (m[static_cast<size_t>(q)] + kTB - 1) / kTB;
+            for (int32_t i = 0; i < L; ++i, ++g) {
+                WavePass& wp = passes[static_cast<size_t>(g / kWarp)];
+                const int l = static_cast<int>(g % kWarp);
+                const uint32_t bit = 1u << l;
+                wp.q[x][l] = q;
+                wp.row0[x][l] = i * kTB;
+                if (i == 0)
+                    wp.first[x] |= bit;
+                else
+                    wp.first[x] &= ~bit;
+                if (i == L - 1) wp.last[x] |= bit;
+            }
+        }
+    }
+    return passes;
+}
+
 // Grows the shared scratch (control block, saturation list, boundary buffers).  Cached plans
 // bake these pointers into their graphs, so a reallocation drops them.
 sw_status ensure_scratch(sw_db* db, size_t flag_cap, size_t bnd_elems, size_t spill_elems) {
@@ -262,9 +308,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     }
 
     // Long subjects of a search with two or more queries: the packed wavefront kernel pairs two
-    // queries per register against one subject (passes of 32 x 8 or 32 x 16 rows; the height
-    // with fewer padded rows, charging about 10 operations of per-step overhead per lane).
-    std::vector<MqStep> wsteps;
+    // queries per register against one subject (passes of 32 x 8, 12 or 16 rows).
+    std::vector<WavePass> wpasses;
     P.wave = wave_enabled() && P.int16_ok && nonempty >= 2 && !db->layout.long_ids.empty() &&
              db->wave_occ[0] > 0 && db->wave_occ[1] > 0 && db->wave_occ[2] > 0;
     if (P.wave) {
@@ -273,8 +318,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         double best_cost = 1e300;
         for (int v = 0; v < 3; ++v) {
             const int T = 32 * kWaveRows[v];
-            const double steps_v = static_cast<double>(build_streams(P.m, order, T).size());
-            const double cost = steps_v * 2.0 * T * (5.5 + 10.0 / kWaveRows[v]);
+            const double passes_v = static_cast<double>(build_wave_passes(P.m, order, kWaveRows[v]).size());
+            const double cost = passes_v * 2.0 * T * (5.5 + 10.0 / kWaveRows[v]);
             if (cost < best_cost * 0.999) {
                 best_cost = cost;
                 P.wave_rows = kWaveRows[v];
@@ -283,9 +328,9 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         const char* wr = std::getenv("SWGB_WAVE_ROWS");
         if (wr && (std::atoi(wr) == 8 || std::atoi(wr) == 12 || std::atoi(wr) == 16)) P.wave_rows = std::atoi(wr);
         const int T = 32 * P.wave_rows;
-        wsteps = build_streams(P.m, order, T);
-        P.num_wsteps = static_cast<int32_t>(wsteps.size());
-        P.wrows_pad = round_up(static_cast<int64_t>(P.num_wsteps) * T, kQpRows);
+        wpasses = build_wave_passes(P.m, order, P.wave_rows);
+        P.num_wpasses = static_cast<int32_t>(wpasses.size());
+        P.wrows_pad = round_up(static_cast<int64_t>(P.num_wpasses) * T, kQpRows);
         const int occ = db->wave_occ[P.wave_rows == 8 ? 0 : P.wave_rows == 12 ? 1 : 2];
         const int64_t items = (static_cast<int64_t>(db->layout.long_ids.size()) + wave_warps() - 1) / wave_warps();
         P.wave_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(items, static_cast<int64_t>(db->sms) * occ)));
@@ -488,7 +533,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         CU(P.pp.ensure(static_cast<size_t>((A + 1) * P.rows_pad)));
     }
     if (P.wave) {
-        CU(P.wsteps.ensure(wsteps.size()));
+        CU(P.wpasses.ensure(wpasses.size()));
         CU(P.wpp.ensure(static_cast<size_t>((A + 1) * P.wrows_pad)));
     }
     std::vector<QueryDesc> descs(static_cast<size_t>(nq));
@@ -512,7 +557,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     if (P.sp)
         CU(cudaMemcpyAsync(P.mt.ptr, mt.data(), sizeof(int16_t) * mt.size(), cudaMemcpyHostToDevice, us));
     if (P.wave)
-        CU(cudaMemcpyAsync(P.wsteps.ptr, wsteps.data(), sizeof(MqStep) * wsteps.size(),
+        CU(cudaMemcpyAsync(P.wpasses.ptr, wpasses.data(), sizeof(WavePass) * wpasses.size(),
                            cudaMemcpyHostToDevice, us));
     CU(cudaStreamSynchronize(us));
 
@@ -568,8 +613,8 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         wp.queries = P.descs.ptr;
         wp.pp = P.wpp.ptr;
         wp.rows_pad = P.wrows_pad;
-        wp.steps = P.wsteps.ptr;
-        wp.num_steps = P.num_wsteps;
+        wp.passes = P.wpasses.ptr;
+        wp.num_passes = P.num_wpasses;
         wp.alphabet1 = A + 1;
         wp.ctrl = db->ctrl.ptr;
         wp.flags = db->flags.ptr;
@@ -681,9 +726,9 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     }
     ++launches;
     if (P.wave) {
-        CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.wsteps.ptr, P.num_wsteps, nullptr,
-                           32 * P.wave_rows, P.matrix.ptr, db->A, P.qp_bias, P.wpp.ptr,
-                           P.wrows_pad, db->ctrl.ptr, st));
+        CU(launch_build_pp_wave(d_queries, P.qoff.ptr, P.wpasses.ptr, P.num_wpasses, P.wave_rows,
+                                P.matrix.ptr, db->A, P.qp_bias, P.wpp.ptr, P.wrows_pad,
+                                db->ctrl.ptr, st));
         ++launches;
     }
     CU(record(db->ev[1], st));

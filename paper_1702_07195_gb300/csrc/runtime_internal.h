@@ -90,9 +90,9 @@ struct Plan {
     bool wave = false;
     int wave_rows = 16;           // query rows per lane
     int wave_grid = 0;
-    int32_t num_wsteps = 0;
+    int32_t num_wpasses = 0;
     int64_t wrows_pad = 0;
-    DevBuf<MqStep> wsteps;
+    DevBuf<WavePass> wpasses;
     DevBuf<uint32_t> wpp;
     WaveParams wave_p{};
     // packed int16x2 wavefront kernel for routed groups of a one-query search (two subjects

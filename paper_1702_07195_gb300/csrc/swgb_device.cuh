@@ -174,20 +174,31 @@ struct IntraParams {
 // Packed int16x2 intra-task wavefront kernel (k_wave.cu).  Two int16 lanes per register:
 //  * two-query mode (queries != two-subject): one subject per warp against two streams of
 //    query passes (pass k of stream a in the low lanes, of stream b in the high lanes; the
-//    pass structure is an MqStep list with rows_per_step = 32 x rows per lane), scores from
-//    the paired profile pp;
+//    pass structure is a WavePass list, 32 x rows per lane rows per pass), scores from the
+//    paired profile pp;
 //  * two-subject mode: one query, the subjects in slots 2t and 2t + 1 of an interleaved group
 //    per warp, scores from the query profile qp (two lookups packed by a byte permute).
+// One pass of the two-query wavefront.  Each of the two streams (a: low int16 halves, b: high)
+// is a chain of queries packed at lane granularity -- a query of m rows takes ceil(m / kTB)
+// consecutive lanes -- cut into passes of 32 lanes, so one pass can hold the end of a query,
+// whole short queries and the start of the next.
+struct WavePass {
+    uint32_t first[2];     // bit l: lane l holds row 0 of its query, or no query (zero boundary above)
+    uint32_t last[2];      // bit l: lane l holds the last row of its query
+    int32_t q[2][32];      // query slot of lane l, -1: none
+    int32_t row0[2][32];   // query row of lane l's first row
+};
+
 struct WaveParams {
     const uint8_t* plain;       // two-query mode: subjects in original order
     const int64_t* plain_off;
     const int32_t* subjects;    // two-query mode: subject ids, longest first
     int64_t num_subjects;
     const QueryDesc* queries;   // score rows (and the profile in two-subject mode)
-    const uint32_t* pp;         // two-query mode: pp[d * rows_pad + k * rows_per_step + r]
+    const uint32_t* pp;         // two-query mode: pp[d * rows_pad + k * 32 kTB + l * kTB + r]
     int64_t rows_pad;
-    const MqStep* steps;
-    int32_t num_steps;
+    const WavePass* passes;     // two-query mode: the passes of the two streams
+    int32_t num_passes;
     int32_t query;              // two-subject mode: the query slot
     const uint8_t* inter;       // two-subject mode: interleaved groups [group_begin, group_end)
     const int64_t* group_off;
@@ -215,6 +226,11 @@ int wave_warps();
 size_t wave_smem_bytes(int rows_per_lane, int alphabet1);
 int wave_occupancy(int rows_per_lane, int alphabet1);
 cudaError_t launch_wave_mq(const WaveParams& p, int rows_per_lane, int grid, cudaStream_t st);
+// Paired profile of the two-query wavefront from its pass list (pp of WaveParams).
+cudaError_t launch_build_pp_wave(const uint8_t* d_queries, const int64_t* d_qoff,
+                                 const WavePass* d_passes, int32_t num_passes, int32_t rows_per_lane,
+                                 const int8_t* d_matrix, int32_t A, int32_t bias, uint32_t* d_pp,
+                                 int64_t rows_pad, Control* ctrl, cudaStream_t st);
 constexpr int kWaveSsRows[2] = {5, 8};  // query rows per lane of the two-subject variants
 // Two-subject mode holds the whole query profile in shared memory (one block of
 // wave_ss_warps() warps per SM): wave_ss_fits says whether a query of m rows fits.

@@ -2,9 +2,10 @@
 long subject; the intra-task scheme of Section 1 on Eqs. sw2-sw4) against the oracle,
 tolerance 0 (integer scores).
 
-Cases: query lengths around the pass heights of both variants (256 and 512 rows), empty and
-one-residue queries, several queries per stream (a half restarts from the zero boundary while
-the other continues), subject lengths around the 32-column blocks of the wavefront, gap-cost
+Cases: query lengths around the pass heights of the variants (256, 384 and 512 rows), empty
+and one-residue queries, several queries per stream (a half restarts from the zero boundary while
+the other continues), many short queries packed several to a pass at lane granularity (queries
+shorter than one lane's rows, queries ending and starting inside a pass), subject lengths around the 32-column blocks of the wavefront, gap-cost
 regimes, small and asymmetric alphabets, planted hits above the int16 range (flagged and
 rescored in int32, with and without overflow of the saturation list), and equality with the
 int32 kernels (SWGB_WAVE=0).
@@ -53,6 +54,7 @@ def _db(rng, n_short=60, long_lens=(33, 63, 64, 65, 95, 96, 97, 200, 511, 1000, 
     [255, 257, 1, 0, 513],            # empty and one-residue queries, ragged passes
     [1024, 700, 512, 511, 300, 90],   # 16 rows per lane, several queries per stream
     [3000, 40],                       # one long stream against a short one
+    [5, 1, 13, 12, 11, 24, 25, 100, 7, 3, 16, 17, 33, 2, 9, 48, 300, 0, 8, 384],   # several per pass
 ])
 @pytest.mark.parametrize("rows", ["8", "12", "16"])
 def test_two_query_wavefront_matches_oracle(sw, qlens, rows, monkeypatch):
