@@ -167,7 +167,7 @@ __device__ __forceinline__ uint2 mask_boundary(uint2 v, unsigned keep, unsigned 
 // takes subjects [i * kWaveBW, (i + 1) * kWaveBW) of the list (longest first), one per warp,
 // and runs every pass of the two-stream pass list over them.
 template <int kTB>
-__global__ void __launch_bounds__(kWaveBW * kWarp, 3) k_wave_mq_i16x2(const WaveParams p) {
+__global__ void __launch_bounds__(kWaveBW * kWarp, (kTB >= 12 ? 2 : 3)) k_wave_mq_i16x2(const WaveParams p) {
     constexpr int kBlock = kWaveBW * kWarp;
     constexpr int kRowsB = kTB * kWarp;
     constexpr int kPStride = slice_stride<kTB>();   // words per residue row of the slice
