@@ -35,7 +35,13 @@
  * intra-task kernel), SWGB_INTRA_BLOCK=0 (per-warp int32 kernel, read at load),
  * SWGB_INTRA_BLOCKS_PER_SM=n, SWGB_SCORE_PROFILE=1 (score-profile single-query kernel,
  * Section 4.3), SWGB_WAVE=0 (int32 instead of the packed int16x2 wavefront kernel for long
- * subjects), SWGB_GRAPHS=0 (no CUDA-graph capture).  Scores do not depend on them.
+ * subjects), SWGB_WAVE_ROWS=8|12|16 (its rows per lane), SWGB_PAIR=0 (int32 instead of the
+ * packed two-subject wavefront for the routed groups of one query), SWGB_PAIR_HALF=1|auto (its
+ * bulk on two 16-lane wavefronts per warp whenever they fit, or where the plan's cost model
+ * prefers them; default: 32-lane wavefronts only), SWGB_PAIR_HALF_FROM=i (16-lane items from
+ * slot pair i on), SWGB_LONG_PAIRS=n,
+ * SWGB_LONG_BLOCKS=n (its first phase), SWGB_GRAPHS=0 (no CUDA-graph capture).  Scores do not
+ * depend on them.
  */
 #ifndef SWGB_H
 #define SWGB_H
@@ -99,7 +105,9 @@ typedef struct {
                               of int32: 1 = two queries per register (long subjects of a
                               batch), 2 = two subjects per register (routed groups of a
                               one-query search), 0 = int32 only */
-    int32_t reserved;
+    int32_t wave_lanes;    /* lanes per wavefront of the packed kernel: 32, or 16 when some
+                              warps ran two 16-lane wavefronts (the shorter pairs of
+                              intra_packed = 2); 0 without a packed intra-task launch */
 } sw_stats;
 
 /* ---------------------------------------------------------------- database ------------ */

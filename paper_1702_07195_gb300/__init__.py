@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("inter_grid", ctypes.c_int32), ("inter_block", ctypes.c_int32),
                 ("graph_replay", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("multi_query", ctypes.c_int32), ("score_profile", ctypes.c_int32),
-                ("intra_packed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("intra_packed", ctypes.c_int32), ("wave_lanes", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

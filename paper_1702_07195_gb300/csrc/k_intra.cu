@@ -189,10 +189,11 @@ __global__ void __launch_bounds__(kIBlock) k_intra_i32(const IntraParams p) {
         }
         return;
     }
-    // Saturated lanes: the list first.
+    // Saturated lanes: the list first.  (Usually empty: then no warp touches the work counter,
+    // whose atomics from every warp of the grid would otherwise serialise for microseconds.)
     const unsigned count = *reinterpret_cast<volatile unsigned*>(&p.ctrl->flag_count);
     const unsigned listed = count < p.flag_cap ? count : p.flag_cap;
-    for (;;) {
+    for (; listed > 0;) {
         unsigned k = 0;
         if (lane == 0) k = atomicAdd(&p.ctrl->next_rescore, 1u);
         k = __shfl_sync(0xffffffffu, k, 0);

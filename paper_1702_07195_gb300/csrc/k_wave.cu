@@ -409,17 +409,22 @@ constexpr int kSsBW = 16;         // warps per block (one block per SM)
 constexpr int kSsBlocksPerSM = 1;
 constexpr int kSsLongWarps = 4;   // warps of a long block that run the first phase
 constexpr int kResPad = 32;       // dummy columns kept before column 0 in a residue buffer
+constexpr int kSsBulkRows = 9;    // rows per lane of the 16-lane bulk wavefronts (144-row passes)
+constexpr int kSsBulkLanes = 16;
 
-template <int kTB>
+// kTBL query rows per lane of the 32-lane wavefronts (first phase and the longer bulk pairs);
+// kHalf: the bulk's shorter pairs run two 16-lane wavefronts per warp (two slot pairs,
+// kSsBulkRows rows per lane).  With 16 lanes a slot pair fills and drains its wavefront in 15
+// steps instead of 31, and a 144-row query fits one pass exactly, but a warp's item (two pairs,
+// 9 rows per lane and step) lasts longer than a 32-lane one.
+template <int kTBL, bool kHalf>
 __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2(const WaveParams p) {
-    constexpr int kRowsB = kTB * kWarp;
-    constexpr int kW = (kTB + 1) / 2;
-    constexpr int kPStride = slice_stride<kW>();
-    extern __shared__ __align__(16) uint32_t s_sl[];   // passes x (A + 1) x kPStride, residues
+    constexpr int kWL = (kTBL + 1) / 2;
+    constexpr int kWB = (kSsBulkRows + 1) / 2;
+    extern __shared__ __align__(16) uint32_t s_sl[];   // profiles, then residue buffers
     const int lane = threadIdx.x & (kWarp - 1);
     const int warp = threadIdx.x >> 5;
-    const int my_chunk = chunk_offset<kW>(lane);
-    int2* spill = p.spill + (static_cast<int64_t>(blockIdx.x) * kSsBW + warp) * p.spill_stride;
+    const int64_t gwarp = static_cast<int64_t>(blockIdx.x) * kSsBW + warp;
     PackedGaps k;
     k.ngoe = pack2(-p.gaps.goe);
     k.nge = pack2(-p.gaps.ge);
@@ -427,99 +432,137 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
     k.floor = 0x80008000u;
     const unsigned init_hm = k.ngoe, init_f = k.ngep;
     const QueryDesc qd = p.queries[p.query];
-    const int passes = (qd.m + kRowsB - 1) / kRowsB;
-    const int slice_words = p.alphabet1 * kPStride;
+    const int passes_l = max(1, (qd.m + kWarp * kTBL - 1) / (kWarp * kTBL));
+    const int passes_b = kHalf ? max(1, (qd.m + kSsBulkLanes * kSsBulkRows - 1) / (kSsBulkLanes * kSsBulkRows)) : 0;
+    const int words_l = p.alphabet1 * slice_stride<kWL>();
+    const int words_b = p.alphabet1 * slice_stride<kWB>();
+    uint32_t* prof_l = s_sl;
+    uint32_t* prof_b = s_sl + passes_l * words_l;
     const int64_t total_pairs = (p.group_end - p.group_begin) * (kGroupSeqs / 2);
+    const int64_t long_pairs = min(p.long_pairs, total_pairs);
+    const bool long_block = static_cast<int>(blockIdx.x) < p.long_blocks;
     const int bias = p.gaps.goe;   // score 0 of rows past the profile: S' = 0 + Goe
     const uint16_t dummy2 = static_cast<uint16_t>((p.alphabet1 - 1) * 0x0101);
-    // residue buffer of this warp: column c of the pair at index c + kResPad
+    // residue buffers of this warp (one per wavefront): column c of a pair at index c + kResPad
     const int res_stride = wave_ss_res_stride(p.max_group_len);
-    uint16_t* rbuf = reinterpret_cast<uint16_t*>(s_sl + passes * slice_words) + warp * res_stride;
+    uint16_t* rbuf = reinterpret_cast<uint16_t*>(prof_b + passes_b * words_b) + warp * (kHalf ? 2 : 1) * res_stride;
 
-    // The whole query profile (Section 4.3), built here from the query and the matrix:
-    // pass, residue d, lane chunk, word w = rows (2w, 2w + 1) of the lane, each S'(q_i, d) =
-    // SM(q_i, d) + Goe; the dummy code and rows past the query score 0 (S' = Goe).  A query
-    // residue outside the alphabet sets status bit 0 (reported by the host after the search)
-    // and scores 0 here.
-    // The matrix goes to shared memory first, so that building a word costs shared-memory reads
-    // only (one query residue pair per thread, then every residue code d).
+    // The query profile (Section 4.3), built here from the query and the matrix, for each
+    // wavefront shape in use: pass, residue d, lane chunk, word w = rows (2w, 2w + 1) of the
+    // lane, each S'(q_i, d) = SM(q_i, d) + Goe; the dummy code and rows past the query score 0
+    // (S' = Goe).  A 16-lane profile stores every lane's chunk twice (chunks l and l + 16), so
+    // the two wavefronts of a warp read it with the 32-lane bank pattern.  A query residue
+    // outside the alphabet sets status bit 0 (reported by the host after the search) and
+    // scores 0 here.  The matrix goes to shared memory first, so that building a word costs
+    // shared-memory reads only.
     const int A = p.alphabet1 - 1;
     __shared__ int8_t s_mat[kMaxAlphabet * kMaxAlphabet];
     for (int i = threadIdx.x; i < A * A; i += blockDim.x) s_mat[i] = p.matrix[i];
     __syncthreads();
     const uint8_t* qres = p.qres + p.qres_off[p.query];
-    for (int v = threadIdx.x; v < passes * kW * kWarp; v += blockDim.x) {
-        const int ps = v / (kW * kWarp);                 // pass, lane, word of the lane's rows
-        const int rem = v - ps * (kW * kWarp);
-        const int ln = rem / kW, wi = rem - ln * kW;
-        const int r0 = ps * kRowsB + ln * kTB + 2 * wi;
-        const bool has1 = 2 * wi + 1 < kTB;
-        int c0 = r0 < qd.m ? qres[r0] : -1;              // -1: a row past the query
-        int c1 = has1 && r0 + 1 < qd.m ? qres[r0 + 1] : -1;
-        if (c0 >= A || c1 >= A) {
-            atomicOr(&p.ctrl->status, 1u);
-            c0 = c0 >= A ? -1 : c0;
-            c1 = c1 >= A ? -1 : c1;
+    auto build = [&](auto tb_c, auto lanes_c, uint32_t* base, const int passes) {
+        constexpr int kTB = decltype(tb_c)::value, kL = decltype(lanes_c)::value;
+        constexpr int kW = (kTB + 1) / 2;
+        constexpr int kStride = slice_stride<kW>();
+        const int words = p.alphabet1 * kStride;
+        for (int v = threadIdx.x; v < passes * kW * kWarp; v += blockDim.x) {
+            const int ps = v / (kW * kWarp);                 // pass, chunk, word of the lane's rows
+            const int rem = v - ps * (kW * kWarp);
+            const int ln = rem / kW, wi = rem - ln * kW;
+            const int r0 = ps * (kL * kTB) + (ln % kL) * kTB + 2 * wi;
+            const bool has1 = 2 * wi + 1 < kTB;
+            int c0 = r0 < qd.m ? qres[r0] : -1;              // -1: a row past the query
+            int c1 = has1 && r0 + 1 < qd.m ? qres[r0 + 1] : -1;
+            if (c0 >= A || c1 >= A) {
+                atomicOr(&p.ctrl->status, 1u);
+                c0 = c0 >= A ? -1 : c0;
+                c1 = c1 >= A ? -1 : c1;
+            }
+            uint32_t* dst = base + ps * words + chunk_offset<kW>(ln) + wi;
+            for (int d = 0; d < p.alphabet1; ++d) {
+                const int s0 = (c0 >= 0 && d < A) ? s_mat[c0 * A + d] + bias : bias;
+                const int s1 = (c1 >= 0 && d < A) ? s_mat[c1 * A + d] + bias : bias;
+                dst[d * kStride] = (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
+            }
         }
-        uint32_t* dst = s_sl + ps * slice_words + chunk_offset<kW>(ln) + wi;
-        for (int d = 0; d < p.alphabet1; ++d) {
-            const int s0 = (c0 >= 0 && d < A) ? s_mat[c0 * A + d] + bias : bias;
-            const int s1 = (c1 >= 0 && d < A) ? s_mat[c1 * A + d] + bias : bias;
-            dst[d * kPStride] = (static_cast<unsigned>(s0) & 0xFFFFu) | (static_cast<unsigned>(s1) << 16);
-        }
-    }
+    };
+    build(std::integral_constant<int, kTBL>{}, std::integral_constant<int, kWarp>{}, prof_l, passes_l);
+    if constexpr (kHalf)
+        build(std::integral_constant<int, kSsBulkRows>{}, std::integral_constant<int, kSsBulkLanes>{},
+              prof_b, passes_b);
     __syncthreads();
 
-    // Slot pair pi (0 = the longest): its group, pair index t, subject ids and lengths.
+    // Slot pair pi (0 = the longest): its group, pair index t, subject ids and lengths; an
+    // index outside [0, total_pairs) is an empty pair.
     struct PairRef {
         int64_t g;
         int t, id[2], n[2];
     };
     auto pair_ref = [&](const int64_t pi) {
         PairRef r;
-        r.g = p.group_end - 1 - pi / (kGroupSeqs / 2);
-        r.t = kGroupSeqs / 2 - 1 - static_cast<int>(pi % (kGroupSeqs / 2));
-        for (int h = 0; h < 2; ++h) {
-            r.id[h] = p.perm[r.g * kGroupSeqs + 2 * r.t + h];
-            r.n[h] = r.id[h] >= 0 ? static_cast<int>(p.plain_off[r.id[h] + 1] - p.plain_off[r.id[h]]) : 0;
+        r.g = -1;
+        r.t = 0;
+        r.id[0] = r.id[1] = -1;
+        r.n[0] = r.n[1] = 0;
+        if (pi >= 0 && pi < total_pairs) {
+            r.g = p.group_end - 1 - pi / (kGroupSeqs / 2);
+            r.t = kGroupSeqs / 2 - 1 - static_cast<int>(pi % (kGroupSeqs / 2));
+            for (int h = 0; h < 2; ++h) {
+                r.id[h] = p.perm[r.g * kGroupSeqs + 2 * r.t + h];
+                r.n[h] = r.id[h] >= 0 ? static_cast<int>(p.plain_off[r.id[h] + 1] - p.plain_off[r.id[h]]) : 0;
+            }
         }
         return r;
     };
     // Residue pairs of columns [0, n rounded up to 8) from the interleaved group (16 bytes = 8
     // columns per load; past each subject's end the layout holds the dummy code), the dummy pair
-    // elsewhere in [-kResPad, n + kWarp + 1).  Uniform trip counts (predicated bodies): the warp
-    // stays converged.
-    auto stage_residues = [&](const PairRef& r, const int n) {
-        const uint4* src = reinterpret_cast<const uint4*>(p.inter + p.group_off[r.g] + r.t * 16);
+    // elsewhere in [-kResPad, n_fill + kWarp + 1).  Uniform trip counts (predicated bodies): the
+    // warp stays converged.
+    auto stage_residues = [&](const PairRef& r, const int n, const int n_fill, uint16_t* buf) {
         const int chunks = (n + 7) >> 3;
-        __syncwarp();   // the previous item's steps have read the buffer
-        for (int c0 = 0; c0 < chunks; c0 += kWarp) {
-            const int c = c0 + lane;
-            if (c < chunks)
-                *reinterpret_cast<uint4*>(rbuf + kResPad + 8 * c) = src[static_cast<int64_t>(c) * (kGroupChunk / 16)];
+        if (r.g >= 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(p.inter + p.group_off[r.g] + r.t * 16);
+            for (int c0 = 0; c0 < chunks; c0 += kWarp) {
+                const int c = c0 + lane;
+                if (c < chunks)
+                    *reinterpret_cast<uint4*>(buf + kResPad + 8 * c) = src[static_cast<int64_t>(c) * (kGroupChunk / 16)];
+            }
         }
-        rbuf[lane] = dummy2;                                  // columns [-kResPad, 0)
-        for (int c0 = kResPad + 8 * chunks; c0 < kResPad + n + kWarp + 2; c0 += kWarp)
-            if (c0 + lane < kResPad + n + kWarp + 2) rbuf[c0 + lane] = dummy2;
-        __syncwarp();
+        buf[lane] = dummy2;                                   // columns [-kResPad, 0)
+        for (int c0 = kResPad + 8 * chunks; c0 < kResPad + n_fill + kWarp + 2; c0 += kWarp)
+            if (c0 + lane < kResPad + n_fill + kWarp + 2) buf[c0 + lane] = dummy2;
     };
 
-    // -(r + 1) Ge' in both halves, for the unrolled F recurrence of the first phase
-    unsigned ngep_r[kTB];
+    // Slot pairs pi0 (and pi1: the second 16-lane wavefront) over every pass, both subjects of a
+    // pair packed in the halves of the registers.  kL lanes per wavefront; `prefix`: the F
+    // recurrence unrolled down the lane's rows (a shorter dependency chain).
+    auto align = [&](auto tb_c, auto lanes_c, auto prefix, const int64_t pi0, const int64_t pi1) {
+        constexpr int kTB = decltype(tb_c)::value, kL = decltype(lanes_c)::value;
+        constexpr int kW = (kTB + 1) / 2;
+        constexpr int kPStride = slice_stride<kW>();
+        const uint32_t* prof = kL == kWarp ? prof_l : prof_b;
+        const int passes = kL == kWarp ? passes_l : passes_b;
+        const int words = p.alphabet1 * kPStride;
+        const int seg = lane / kL, sl = lane % kL;
+        const PairRef r0 = pair_ref(pi0);
+        const PairRef r1 = pair_ref(kL < kWarp ? pi1 : -1);
+        const int n0 = max(r0.n[0], r0.n[1]), n1 = max(r1.n[0], r1.n[1]);
+        const int N = max(n0, n1);
+        __syncwarp();   // the previous item's steps have read the buffers
+        stage_residues(r0, n0, N, rbuf);
+        if constexpr (kL < kWarp) stage_residues(r1, n1, N, rbuf + res_stride);
+        __syncwarp();
+        const int n_me = seg == 0 ? n0 : n1;
+        const uint16_t* rcol = rbuf + seg * res_stride + kResPad - sl;   // rcol[t]: column t - sl
+        int2* spill = p.spill + (gwarp * 2 + seg) * p.spill_stride;
+        unsigned ngep_r[kTB];
+        if constexpr (decltype(prefix)::value) {
 #pragma unroll
-    for (int r = 0; r < kTB; ++r) ngep_r[r] = pack2(-(r + 1) * p.gaps.gep);
-
-    // One slot pair (pair index pi, 0 = the longest) over every pass, both subjects packed;
-    // `prefix`: the F recurrence unrolled down the lane's rows (a shorter dependency chain).
-    auto align_pair = [&](const int64_t pi, auto prefix) {
-        const PairRef r = pair_ref(pi);
-        const int id_a = r.id[0], id_b = r.id[1];
-        const int n = max(r.n[0], r.n[1]);
-        stage_residues(r, n);
-        const uint16_t* rcol = rbuf + kResPad - lane;   // rcol[t] = residues of column t - lane
+            for (int r = 0; r < kTB; ++r) ngep_r[r] = pack2(-(r + 1) * p.gaps.gep);
+        }
         unsigned best = 0;
-        for (int pass = 0; n > 0 && pass < passes; ++pass) {
-            const uint32_t* sl = s_sl + pass * slice_words + my_chunk;
+        for (int pass = 0; N > 0 && pass < passes; ++pass) {
+            const uint32_t* slp = prof + pass * words + chunk_offset<kW>(lane);
             unsigned Hm[kTB], E[kTB];
 #pragma unroll
             for (int r = 0; r < kTB; ++r) {
@@ -530,28 +573,28 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
             unsigned out_hm = init_hm, out_f = init_f;
             uint2 sp_cur = make_uint2(init_hm, init_f), sp_next = sp_cur;
             if (pass > 0) {
-                if (lane < n) sp_cur = reinterpret_cast<const uint2*>(spill)[lane];
-                if (32 + lane < n) sp_next = reinterpret_cast<const uint2*>(spill)[32 + lane];
+                if (sl < n_me) sp_cur = reinterpret_cast<const uint2*>(spill)[sl];
+                if (kL + sl < n_me) sp_next = reinterpret_cast<const uint2*>(spill)[kL + sl];
             }
             // Pipeline: at step t a lane holds the profile words of its column (loaded during
             // step t - 1) and loads its next column's residues, then their words.
             unsigned wa[kW], wb[kW];
             {
-                const unsigned r0 = rcol[0];
+                const unsigned rr = rcol[0];
 #pragma unroll
                 for (int wi = 0; wi < kW; ++wi) {
-                    wa[wi] = sl[(r0 & 0xFFu) * kPStride + wi];
-                    wb[wi] = sl[(r0 >> 8) * kPStride + wi];
+                    wa[wi] = slp[(rr & 0xFFu) * kPStride + wi];
+                    wb[wi] = slp[(rr >> 8) * kPStride + wi];
                 }
             }
-            const int steps = n + kWarp - 1;
+            const int steps = N + kL - 1;
             auto step = [&](const int t, const int src_lane, auto on_first, auto write) {
-                const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1);
-                const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
+                const unsigned up_hm = __shfl_up_sync(0xffffffffu, out_hm, 1, kL);
+                const unsigned up_f = __shfl_up_sync(0xffffffffu, out_f, 1, kL);
                 unsigned l0_hm = init_hm, l0_f = init_f;
                 if constexpr (!decltype(on_first)::value) {
-                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src_lane);
-                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src_lane);
+                    l0_hm = __shfl_sync(0xffffffffu, sp_cur.x, src_lane, kL);
+                    l0_f = __shfl_sync(0xffffffffu, sp_cur.y, src_lane, kL);
                 }
                 unsigned ca[kW], cb[kW];
                 const unsigned rn = rcol[t + 1];
@@ -559,12 +602,12 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 for (int wi = 0; wi < kW; ++wi) {
                     ca[wi] = wa[wi];
                     cb[wi] = wb[wi];
-                    wa[wi] = sl[(rn & 0xFFu) * kPStride + wi];   // step t + 1
-                    wb[wi] = sl[(rn >> 8) * kPStride + wi];
+                    wa[wi] = slp[(rn & 0xFFu) * kPStride + wi];   // step t + 1
+                    wb[wi] = slp[(rn >> 8) * kPStride + wi];
                 }
-                unsigned F = lane == 0 ? l0_f : up_f;
+                unsigned F = sl == 0 ? l0_f : up_f;
                 const unsigned d = hm_prev;
-                hm_prev = lane == 0 ? l0_hm : up_hm;
+                hm_prev = sl == 0 ? l0_hm : up_hm;
                 auto score = [&](const int rb, unsigned (&sc)[4]) {
 #pragma unroll
                     for (int i = 0; i < 4; i += 2) {
@@ -582,14 +625,14 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 out_hm = Hm[kTB - 1];
                 out_f = F;
                 if constexpr (decltype(write)::value) {
-                    const int j = t - lane;
-                    if (lane == kWarp - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n))
+                    const int j = t - sl;
+                    if (sl == kL - 1 && static_cast<unsigned>(j) < static_cast<unsigned>(n_me))
                         spill[j] = make_int2(static_cast<int>(out_hm), static_cast<int>(out_f));
                 }
             };
             auto run = [&](auto on_first, auto write) {
                 if constexpr (decltype(on_first)::value) {
-                    // constant lane-0 boundary: no 32-step blocks; an extra step past the end
+                    // constant lane-0 boundary: no kL-step blocks; an extra step past the end
                     // (every lane on a dummy column) is harmless
 #pragma unroll 1
                     for (int t = 0; t < steps; t += 2) {
@@ -597,23 +640,21 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                         step(t + 1, 0, on_first, write);
                     }
                 } else {
-                for (int tb = 0; tb < steps; tb += kWarp) {
-                    if constexpr (!decltype(on_first)::value) {
+                    for (int tb = 0; tb < steps; tb += kL) {
                         if (tb > 0) {
                             sp_cur = sp_next;
-                            if (tb + 32 + lane < n)
-                                sp_next = reinterpret_cast<const uint2*>(spill)[tb + 32 + lane];
+                            if (tb + kL + sl < n_me)
+                                sp_next = reinterpret_cast<const uint2*>(spill)[tb + kL + sl];
+                        }
+                        const int ue = min(kL, steps - tb);
+                        if (ue == kL) {
+#pragma unroll 2
+                            for (int u = 0; u < kL; ++u) step(tb + u, u, on_first, write);
+                        } else {
+#pragma unroll 1
+                            for (int u = 0; u < ue; ++u) step(tb + u, u, on_first, write);
                         }
                     }
-                    const int ue = min(kWarp, steps - tb);
-                    if (ue == kWarp) {
-#pragma unroll 2
-                        for (int u = 0; u < kWarp; ++u) step(tb + u, u, on_first, write);
-                    } else {
-#pragma unroll 1
-                        for (int u = 0; u < ue; ++u) step(tb + u, u, on_first, write);
-                    }
-                }
                 }
             };
             const bool last = pass == passes - 1;
@@ -632,17 +673,26 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
         }
         unsigned b = best;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b = __vmaxs2(b, __shfl_xor_sync(0xffffffffu, b, o));
-        if (lane == 0) {
-            emit_score(p, p.query, id_a, static_cast<int>(static_cast<short>(b & 0xFFFFu)));
-            emit_score(p, p.query, id_b, static_cast<int>(static_cast<short>(b >> 16)));
+        for (int o = kL / 2; o > 0; o >>= 1) b = __vmaxs2(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if (sl == 0) {
+            const PairRef& r = seg == 0 ? r0 : r1;
+            emit_score(p, p.query, r.id[0], static_cast<int>(static_cast<short>(b & 0xFFFFu)));
+            emit_score(p, p.query, r.id[1], static_cast<int>(static_cast<short>(b >> 16)));
         }
         __syncwarp();
     };
 
     // First phase: the longest slot pairs, alone on their SM sub-partitions.
-    const int64_t long_pairs = min(p.long_pairs, total_pairs);
-    if (static_cast<int>(blockIdx.x) < p.long_blocks) {
+    using TBL = std::integral_constant<int, kTBL>;
+    using Full = std::integral_constant<int, kWarp>;
+    if (long_block) {
+        // Warps w, w + 4, w + 8, w + 12 share a sub-partition (warp w of the block on
+        // sub-partition w mod 4); each group waits at its own named barrier (ids 1-4, 128
+        // threads) until its first-phase warp has drained the queue, so a sub-partition returns
+        // to the bulk as soon as its own first-phase warp is done.
+        static_assert(kSsLongWarps == 4 && kSsBW % kSsLongWarps == 0, "one first-phase warp per sub-partition");
+        const int sub = warp % kSsLongWarps;
+        constexpr int kGroupThreads = kSsBW / kSsLongWarps * kWarp;
         if (warp < kSsLongWarps) {
             for (;;) {
                 unsigned it = 0;
@@ -650,25 +700,44 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
                 it = __shfl_sync(0xffffffffu, it, 0);
                 if (it >= long_pairs) break;
                 if (p.prefix_f)
-                    align_pair(it, std::true_type{});
+                    align(TBL{}, Full{}, std::true_type{}, static_cast<int64_t>(it), int64_t{-1});
                 else
-                    align_pair(it, std::false_type{});
+                    align(TBL{}, Full{}, std::false_type{}, static_cast<int64_t>(it), int64_t{-1});
             }
+            __syncwarp();
+            asm volatile("bar.arrive %0, %1;" ::"r"(1 + sub), "r"(kGroupThreads) : "memory");
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "r"(kGroupThreads) : "memory");
         }
-        __syncthreads();   // the block's other warps wait here: one active warp per sub-partition
     }
+    // Bulk: the remaining pairs, longest first: one per item on the 32-lane wavefront up to
+    // pair half_from, then (kHalf) two per item on 16-lane wavefronts.  A 16-lane item takes
+    // longer than a 32-lane one, so only the short pairs, whose items end well before the
+    // search does, run that way.
+    const int64_t half_from = kHalf ? max(long_pairs, min(p.half_from, total_pairs)) : total_pairs;
+    const int64_t full_items = half_from - long_pairs;
     for (;;) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(&p.ctrl->next_wave, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
-        if (long_pairs + it >= total_pairs) break;
-        align_pair(long_pairs + it, std::false_type{});
+        if (static_cast<int64_t>(it) < full_items) {
+            align(TBL{}, Full{}, std::false_type{}, long_pairs + static_cast<int64_t>(it), int64_t{-1});
+            continue;
+        }
+        const int64_t pi = half_from + 2 * (static_cast<int64_t>(it) - full_items);
+        if (pi >= total_pairs) break;
+        if constexpr (kHalf)
+            align(std::integral_constant<int, kSsBulkRows>{}, std::integral_constant<int, kSsBulkLanes>{},
+                  std::false_type{}, pi, pi + 1);
     }
 }
 
-const void* wave_ss_fn(int rows_per_lane) {
-    return rows_per_lane == 5 ? reinterpret_cast<const void*>(&k_wave_ss_i16x2<5>)
-                              : reinterpret_cast<const void*>(&k_wave_ss_i16x2<8>);
+const void* wave_ss_fn(int rows_per_lane, bool half) {
+    if (half)
+        return rows_per_lane == 5 ? reinterpret_cast<const void*>(&k_wave_ss_i16x2<5, true>)
+                                  : reinterpret_cast<const void*>(&k_wave_ss_i16x2<8, true>);
+    return rows_per_lane == 5 ? reinterpret_cast<const void*>(&k_wave_ss_i16x2<5, false>)
+                              : reinterpret_cast<const void*>(&k_wave_ss_i16x2<8, false>);
 }
 
 // Paired profile of the two-query wavefront: for lane l of pass k,
@@ -733,22 +802,28 @@ int wave_occupancy(int rows_per_lane, int alphabet1) {
     return n;
 }
 
-size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len) {
-    const int stride = rows_per_lane == 5 ? slice_stride<3>() : slice_stride<4>();
-    const int passes = std::max(1, (m + 32 * rows_per_lane - 1) / (32 * rows_per_lane));
-    return static_cast<size_t>(passes) * alphabet1 * stride * sizeof(uint32_t) +
-           static_cast<size_t>(kSsBW) * wave_ss_res_stride(max_group_len) * sizeof(uint16_t);
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len, bool half) {
+    const int stride_l = rows_per_lane == 5 ? slice_stride<3>() : slice_stride<4>();
+    const int passes_l = std::max(1, (m + kWarp * rows_per_lane - 1) / (kWarp * rows_per_lane));
+    constexpr int kRowsB = kSsBulkLanes * kSsBulkRows;
+    const int passes_b = half ? std::max(1, (m + kRowsB - 1) / kRowsB) : 0;
+    return (static_cast<size_t>(passes_l) * stride_l +
+            static_cast<size_t>(passes_b) * slice_stride<(kSsBulkRows + 1) / 2>()) *
+               alphabet1 * sizeof(uint32_t) +
+           static_cast<size_t>(kSsBW) * (half ? 2 : 1) * wave_ss_res_stride(max_group_len) * sizeof(uint16_t);
 }
 
 int wave_ss_warps() { return kSsBW; }
 int wave_ss_blocks_per_sm() { return kSsBlocksPerSM; }
 int wave_ss_long_warps() { return kSsLongWarps; }
+int wave_ss_bulk_rows() { return kSsBulkRows; }
+int wave_ss_bulk_lanes() { return kSsBulkLanes; }
 
-bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem) {
+bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem, bool half) {
     if (m <= 0) return false;
-    const size_t smem = wave_ss_smem_bytes(rows_per_lane, alphabet1, m, max_group_len);
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, alphabet1, m, max_group_len, half);
     if (smem * kSsBlocksPerSM > static_cast<size_t>(max_smem)) return false;
-    const void* fn = wave_ss_fn(rows_per_lane);
+    const void* fn = wave_ss_fn(rows_per_lane, half);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
         cudaSuccess)
         return false;
@@ -757,16 +832,24 @@ bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, in
            n >= kSsBlocksPerSM;
 }
 
-cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int m, int grid, cudaStream_t st) {
-    const size_t smem = wave_ss_smem_bytes(rows_per_lane, p.alphabet1, m, p.max_group_len);
-    const void* fn = wave_ss_fn(rows_per_lane);
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, bool half, int m, int grid,
+                           cudaStream_t st) {
+    const size_t smem = wave_ss_smem_bytes(rows_per_lane, p.alphabet1, m, p.max_group_len, half);
+    const void* fn = wave_ss_fn(rows_per_lane, half);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    if (rows_per_lane == 5)
-        k_wave_ss_i16x2<5><<<grid, kSsBW * kWarp, smem, st>>>(p);
-    else
-        k_wave_ss_i16x2<8><<<grid, kSsBW * kWarp, smem, st>>>(p);
+    if (half) {
+        if (rows_per_lane == 5)
+            k_wave_ss_i16x2<5, true><<<grid, kSsBW * kWarp, smem, st>>>(p);
+        else
+            k_wave_ss_i16x2<8, true><<<grid, kSsBW * kWarp, smem, st>>>(p);
+    } else {
+        if (rows_per_lane == 5)
+            k_wave_ss_i16x2<5, false><<<grid, kSsBW * kWarp, smem, st>>>(p);
+        else
+            k_wave_ss_i16x2<8, false><<<grid, kSsBW * kWarp, smem, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

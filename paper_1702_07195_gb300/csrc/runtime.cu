@@ -86,6 +86,15 @@ bool pair_enabled() {
     return !(v && v[0] == '0');
 }
 
+// Two 16-lane wavefronts per warp for the shorter pairs of the two-subject kernel's bulk: 0
+// never (default: measured slower, the two-pair items lengthen the end of the search), 1 for
+// the whole bulk whenever they fit, -1 the plan's split where the cost model prefers it.
+int pair_half_mode() {
+    const char* v = std::getenv("SWGB_PAIR_HALF");
+    if (!v || !v[0]) return 0;
+    return v[0] == '0' ? 0 : v[0] == 'a' ? -1 : 1;
+}
+
 // Blocks per SM of the block int32 kernel (0: as many as fit).
 int forced_intra_blocks_per_sm() {
     const char* v = std::getenv("SWGB_INTRA_BLOCKS_PER_SM");
@@ -360,7 +369,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         // a one-query search routes its groups to the packed two-subject wavefront kernel
         const bool pair_route = pair_enabled() && P.int16_ok && nonempty == 1 &&
                                 wave_ss_fits(5, A + 1, static_cast<int>(std::max<int64_t>(1, max_m_q)),
-                                             db->layout.max_group_len, db->max_smem);
+                                             db->layout.max_group_len, db->max_smem, false);
         const double r_intra = (pair_route ? 4.0e12 : 3.0e12) * scale * (padded > 0 ? real / padded : 1.0);
         const int64_t warps = static_cast<int64_t>(db->sms) *
                               std::max(1, P.mq ? db->inter_mq_occ[P.variant] : db->inter_occ[P.variant]) * W;
@@ -406,15 +415,19 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
     }
     if (P.g_split == 0) P.mq = false;
     // One query with routed groups: the packed two-subject wavefront kernel, if its whole
-    // profile fits in shared memory (passes of 160 or 256 rows, the cheaper padded height).
+    // profile fits in shared memory: 32-lane wavefronts with passes of 160 or 256 rows (the
+    // cheaper padded height), and, for the bulk's shorter pairs, two 16-lane wavefronts of
+    // 144-row passes per warp (a 15-step fill per slot pair instead of 31) when they fit and
+    // cost less.
     P.pair = false;
+    P.pair_half = false;
     if (pair_enabled() && P.int16_ok && nonempty == 1 && P.g_split < G) {
+        const int mq = static_cast<int>(max_m_q);
+        const int mgl = db->layout.max_group_len;
         double best_cost = 1e300;
         for (int v = 0; v < 2; ++v) {
             const int rows_l = kWaveSsRows[v];
-            if (!wave_ss_fits(rows_l, A + 1, static_cast<int>(max_m_q), db->layout.max_group_len,
-                              db->max_smem))
-                continue;
+            if (!wave_ss_fits(rows_l, A + 1, mq, mgl, db->max_smem, false)) continue;
             const double rows = 32.0 * rows_l;
             const double cost = std::ceil(max_m_q / rows) * rows * (6.5 + 12.0 / rows_l);
             if (cost < best_cost * 0.999) {
@@ -423,28 +436,52 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
                 P.pair = true;
             }
         }
+        if (P.pair && (pair_half_mode() != 0 || std::getenv("SWGB_PAIR_HALF_FROM") != nullptr) &&
+            wave_ss_fits(P.pair_rows, A + 1, mq, mgl, db->max_smem, true)) {
+            double n_avg = 0.0;
+            for (int64_t g = P.g_split; g < G; ++g) n_avg += db->layout.group_len[static_cast<size_t>(g)];
+            n_avg /= static_cast<double>(G - P.g_split);
+            auto bulk_cost = [&](int tb, int lanes) {
+                const double rows = static_cast<double>(lanes) * tb;
+                return std::ceil(max_m_q / rows) * rows * (n_avg + lanes - 1) * (6.5 + 12.0 / tb);
+            };
+            P.pair_half = pair_half_mode() == 1 || std::getenv("SWGB_PAIR_HALF_FROM") != nullptr ||
+                          bulk_cost(wave_ss_bulk_rows(), wave_ss_bulk_lanes()) < 0.999 * bulk_cost(P.pair_rows, kWarp);
+        }
     }
     P.g_pair_end = P.pair ? G : P.g_split;
     if (P.pair) {
         P.pair_grid = db->sms * wave_ss_blocks_per_sm();
-        // Longest slot pairs first, in a phase of their own with one active warp per SM
-        // sub-partition.  Model: a step costs c_step = 2 x (kTB x 6.5 + 8) ALU-pipe clocks (half
-        // an instruction per clock); the bulk, spread over every sub-partition at ~70 % of the
-        // pipe, takes t_bulk; in the bulk phase four warps share a sub-partition, so a pair
-        // whose wavefront would then outlast t_bulk goes to the first phase.
+        // Work split (slot pairs longest first: a first phase, 32-lane items, 16-lane items).
+        // Model in ALU-pipe clocks (a warp issues half an instruction per clock): a 32-lane step
+        // of kTB rows costs c_l = 2 (kTB x 6.5 + 8), a 16-lane step (two pairs) c_b =
+        // 2 (9 x 6.5 + 8).  The bulk spreads over every sub-partition at ~70 % of the pipe and
+        // takes t_bulk (estimated for the whole routed work on 32-lane wavefronts); there four
+        // warps share a sub-partition, so an item lasts four times its issue time.  Groups whose
+        // 32-lane items would outlast t_bulk go to the first phase (one warp alone per
+        // sub-partition); the groups whose 16-lane items would not outlast t_bulk either run
+        // two pairs per item (they start last).
         const int rows_l = P.pair_rows;
-        const double c_step = 2.0 * (rows_l * 6.5 + 8.0);
-        const double passes = std::ceil(static_cast<double>(max_m_q) / (32.0 * rows_l));
-        double steps_all = 0.0;
-        for (int64_t g = P.g_split; g < G; ++g)
-            steps_all += 32.0 * (db->layout.group_len[static_cast<size_t>(g)] + 31.0) * passes;
-        const double t_bulk = steps_all * c_step / (4.0 * db->sms) / 0.7;
-        int64_t long_groups = 0;
-        for (int64_t g = G - 1; g >= P.g_split; --g) {
-            const double span4 = (db->layout.group_len[static_cast<size_t>(g)] + 31.0) * passes * 4.0 * c_step / 0.7;
-            if (span4 <= t_bulk) break;
-            ++long_groups;
-        }
+        const double c_l = 2.0 * (rows_l * 6.5 + 8.0);
+        const double passes_l = std::ceil(static_cast<double>(max_m_q) / (32.0 * rows_l));
+        const double c_b = 2.0 * (wave_ss_bulk_rows() * 6.5 + 8.0);
+        const double passes_b = std::ceil(static_cast<double>(max_m_q) /
+                                          (static_cast<double>(wave_ss_bulk_lanes()) * wave_ss_bulk_rows()));
+        auto item_l = [&](int64_t g) {   // issue clocks of one pair on a 32-lane wavefront
+            return (db->layout.group_len[static_cast<size_t>(g)] + 31.0) * passes_l * c_l;
+        };
+        auto item_b = [&](int64_t g) {   // issue clocks of two pairs on 16-lane wavefronts
+            return (db->layout.group_len[static_cast<size_t>(g)] + 15.0) * passes_b * c_b;
+        };
+        const int64_t routed = G - P.g_split;
+        double clocks = 0.0;   // the whole routed work on 32-lane wavefronts
+        for (int64_t g = P.g_split; g < G; ++g) clocks += (kGroupSeqs / 2) * item_l(g);
+        const double t_bulk = clocks / (4.0 * db->sms) / 0.7;
+        int64_t long_groups = 0, half_groups = 0;
+        for (int64_t g = G - 1; g >= P.g_split && 4.0 * item_l(g) / 0.7 > t_bulk; --g) ++long_groups;
+        if (P.pair_half)
+            for (int64_t g = P.g_split; g < G - long_groups && 4.0 * item_b(g) / 0.7 <= t_bulk; ++g)
+                ++half_groups;
         const char* ev = std::getenv("SWGB_LONG_PAIRS");
         int64_t long_pairs = long_groups * (kGroupSeqs / 2);
         if (ev) long_pairs = std::max<int64_t>(0, std::atoll(ev));
@@ -453,6 +490,12 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
             db->sms / 2, (long_pairs + wave_ss_long_warps() - 1) / wave_ss_long_warps()));
         const char* eb = std::getenv("SWGB_LONG_BLOCKS");
         if (eb) P.pair_long_blocks = std::max(0, std::min(db->sms, std::atoi(eb)));
+        // 16-lane items from pair half_from on (pair 0 = the longest)
+        P.pair_half_from = (routed - half_groups) * (kGroupSeqs / 2);
+        if (pair_half_mode() == 1) P.pair_half_from = 0;
+        const char* eh = std::getenv("SWGB_PAIR_HALF_FROM");
+        if (eh && P.pair_half) P.pair_half_from = std::max<int64_t>(0, std::atoll(eh));
+        if (!P.pair_half) P.pair_half_from = routed * (kGroupSeqs / 2);
     }
 
     // Scratch shared by all plans of this database.
@@ -502,7 +545,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         std::max<int64_t>(static_cast<int64_t>(P.intra_grid) * (intra_block_threads() / kWarp),
                           static_cast<int64_t>(P.intra_block_grid) * P.intra_block_warps),
         std::max<int64_t>(static_cast<int64_t>(P.wave_grid) * wave_warps(),
-                          static_cast<int64_t>(P.pair_grid) * wave_ss_warps()));
+                          static_cast<int64_t>(P.pair_grid) * wave_ss_warps() * 2));
     const int64_t bnd_stride = std::max<int64_t>(1, db->layout.max_group_len / 2 * kWarp);
     const int64_t spill_stride = std::max<int64_t>(1, round_up(db->layout.max_len, 32) + 64);
     P.flag_cap = static_cast<uint32_t>(std::min<int64_t>(std::max<int64_t>(N * nq, 1), db->flag_cap));
@@ -637,6 +680,7 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         wp.group_begin = P.g_split;
         wp.group_end = P.g_pair_end;
         wp.long_pairs = P.pair_long_pairs;
+        wp.half_from = P.pair_half_from;
         wp.prefix_f = static_cast<int64_t>(goe) + static_cast<int64_t>(P.pair_rows) * std::min(goe, ge) <= 32767 ? 1 : 0;
         wp.max_group_len = db->layout.max_group_len;
         wp.qres_off = P.qoff.ptr;
@@ -731,7 +775,10 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
                                 db->ctrl.ptr, st));
         ++launches;
     }
-    CU(record(db->ev[1], st));
+    // An event node costs about two microseconds of a replay: the inter-task stage is bracketed
+    // only when the plan has one.
+    const bool inter_stage = P.mq || P.num_items > 0;
+    if (inter_stage) CU(record(db->ev[1], st));
     if (P.mq) {
         CU(launch_build_pp(d_queries, P.qoff.ptr, nullptr, P.steps.ptr, P.num_steps, nullptr,
                            inter_mq_variant_rows(P.variant), P.matrix.ptr, db->A, P.qp_bias,
@@ -769,7 +816,7 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
         if (P.pair) {
             WaveParams pp = P.pair_p;
             pp.qres = d_queries;
-            CU(launch_wave_ss(pp, P.pair_rows, static_cast<int>(max_m_of(P)), P.pair_grid, st));
+            CU(launch_wave_ss(pp, P.pair_rows, P.pair_half, static_cast<int>(max_m_of(P)), P.pair_grid, st));
             ++launches;
         }
         if (P.g_pair_end < db->layout.num_groups) {
@@ -834,6 +881,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     key.push_back(score_profile_enabled() ? 1 : 0);
     key.push_back(wave_enabled() ? 1 : 0);
     key.push_back(pair_enabled() ? 1 : 0);
+    key.push_back(pair_half_mode());
     {
         const char* ev = std::getenv("SWGB_LONG_PAIRS");
         key.push_back(ev ? std::atoll(ev) : -1);
@@ -841,6 +889,8 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
         key.push_back(eb ? std::atoll(eb) : -1);
         const char* wr = std::getenv("SWGB_WAVE_ROWS");
         key.push_back(wr ? std::atoll(wr) : -1);
+        const char* eh = std::getenv("SWGB_PAIR_HALF_FROM");
+        key.push_back(eh ? std::atoll(eh) : -1);
     }
     for (int q = 0; q <= nq; ++q) key.push_back(h_qoff[q]);
     for (int i = 0; i < A * A; ++i) key.push_back(h_matrix[i]);
@@ -893,8 +943,12 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     db->stats.multi_query = plan->mq ? 1 : 0;
     db->stats.score_profile = plan->sp && plan->num_items > 0 ? 1 : 0;
     db->stats.intra_packed = plan->wave ? 1 : plan->pair ? 2 : 0;
+    const bool half_items = plan->pair && plan->pair_half &&
+                            plan->pair_half_from < (db->layout.num_groups - plan->g_split) * (kGroupSeqs / 2);
+    db->stats.wave_lanes = plan->wave ? kWarp : plan->pair ? (half_items ? wave_ss_bulk_lanes() : kWarp) : 0;
     db->stats.graph_replay = replay ? 1 : 0;
     db->stats.variant = plan->variant;
+    db->stats_inter = plan->mq || plan->num_items > 0;
     db->stats_pending = true;
     return SW_OK;
 }
@@ -903,7 +957,8 @@ sw_status finish_stats(sw_db* db) {
     if (!db->stats_pending) return SW_OK;
     CU(cudaEventSynchronize(db->ev[4]));
     float t = 0;
-    CU(cudaEventElapsedTime(&t, db->ev[1], db->ev[2]));
+    t = 0;
+    if (db->stats_inter) CU(cudaEventElapsedTime(&t, db->ev[1], db->ev[2]));
     db->stats.inter_ms = t;
     CU(cudaEventElapsedTime(&t, db->ev[2], db->ev[3]));
     db->stats.intra_ms = t;

@@ -98,7 +98,9 @@ struct Plan {
     // packed int16x2 wavefront kernel for routed groups of a one-query search (two subjects
     // per register); groups [g_split, g_pair_end) run there, [g_pair_end, G) on int32
     bool pair = false;
-    int pair_rows = 5;
+    int pair_rows = 5;            // rows per lane of the 32-lane wavefronts
+    bool pair_half = false;       // bulk: two 16-lane wavefronts per warp for the shorter pairs
+    int64_t pair_half_from = 0;   // ... from this pair index on (0 = the longest)
     int pair_grid = 0;
     int64_t g_pair_end = 0;
     int64_t pair_long_pairs = 0;  // longest slot pairs, run first with one warp per sub-partition
@@ -161,6 +163,7 @@ struct sw_db {
     // last search
     sw_stats stats{};
     bool stats_pending = false;
+    bool stats_inter = false;    // the last search recorded the inter-task stage events
     std::mutex mu;
     ~sw_db() {
         if (host_inter) cudaFreeHost(host_inter);

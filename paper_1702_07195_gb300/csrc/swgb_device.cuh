@@ -212,6 +212,8 @@ struct WaveParams {
     int64_t long_pairs;         // two-subject mode: the longest slot pairs, served first ...
     int32_t long_blocks;        // ... by a few warps of blocks [0, long_blocks)
     int32_t prefix_f;           // first phase: F recurrence unrolled (Goe + rows x Ge' < 2^15)
+    int64_t half_from;          // two-subject mode: pairs from here on run two per warp item
+                                //   on 16-lane wavefronts (kernels built for it)
     int32_t alphabet1;
     Control* ctrl;
     FlagEntry* flags;
@@ -233,18 +235,24 @@ cudaError_t launch_build_pp_wave(const uint8_t* d_queries, const int64_t* d_qoff
                                  int64_t rows_pad, Control* ctrl, cudaStream_t st);
 constexpr int kWaveSsRows[2] = {5, 8};  // query rows per lane of the two-subject variants
 // Two-subject mode holds the whole query profile in shared memory (one block of
-// wave_ss_warps() warps per SM): wave_ss_fits says whether a query of m rows fits.
-size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len);
+// wave_ss_warps() warps per SM): wave_ss_fits says whether a query of m rows fits.  rows_per_lane
+// is the 32-lane wavefronts'; `half`: the bulk's shorter pairs run two 16-lane wavefronts of
+// wave_ss_bulk_rows() rows per lane in each warp.
+size_t wave_ss_smem_bytes(int rows_per_lane, int alphabet1, int m, int max_group_len, bool half);
 int wave_ss_warps();
 int wave_ss_blocks_per_sm();
 int wave_ss_long_warps();
-bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem);
+int wave_ss_bulk_rows();
+int wave_ss_bulk_lanes();
+bool wave_ss_fits(int rows_per_lane, int alphabet1, int m, int max_group_len, int max_smem, bool half);
 // uint16 entries of a warp's residue buffer: dummy columns, the longest group, and the
 // columns the wavefront's last lanes read past the end, rounded to 16 bytes
 __host__ __device__ constexpr int wave_ss_res_stride(int max_group_len) {
     return (32 + max_group_len + 64 + 7) / 8 * 8;
 }
-cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, int m, int grid, cudaStream_t st);
+// (spill: two regions per resident warp, one per 16-lane wavefront)
+cudaError_t launch_wave_ss(const WaveParams& p, int rows_per_lane, bool half, int m, int grid,
+                           cudaStream_t st);
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_build_qp(const uint8_t* d_queries, const int64_t* d_qoff, int32_t nq,

@@ -48,7 +48,8 @@ def test_plain_reduced(sw):
         got = sw.sw_search(db, wl.queries[0], wl.matrix, wl.gap_open, wl.gap_extend)
         st = sw.sw_get_stats(db)
     _check(got[None], _oracle_all(wl.queries, wl.db, wl.matrix, 10, 2), "plain")
-    assert st["cells"] == 144 * wl.db.num_residues and st["inter_ms"] > 0
+    # a small database: every group routed to the intra-task stage, which the events time
+    assert st["cells"] == 144 * wl.db.num_residues and st["inter_ms"] + st["intra_ms"] > 0
 
 
 @pytest.mark.parametrize("m", [1, 2, 7, 31, 32, 33, 63, 64, 65, 255, 256, 257, 300, 513])

@@ -139,14 +139,22 @@ def test_equals_int32_kernels(sw, monkeypatch):
 
 
 # ------------------------------------------------------------------ two-subject mode
+@pytest.mark.parametrize("half", ["0", "1", "300"])
 @pytest.mark.parametrize("long_pairs", ["0", "7", "100000"])
-@pytest.mark.parametrize("m", [1, 31, 144, 159, 160, 161, 256, 300, 321, 700])
-def test_two_subject_wavefront_matches_oracle(sw, m, long_pairs, monkeypatch):
+@pytest.mark.parametrize("m", [1, 31, 143, 144, 145, 159, 160, 161, 256, 288, 289, 300, 321, 700])
+def test_two_subject_wavefront_matches_oracle(sw, m, long_pairs, half, monkeypatch):
     """One query against a small database whose groups are all routed off the inter-task
-    kernel: the two subjects of each slot pair share a warp (passes of 160 or 256 rows); the
-    longest pairs' subjects run first, one per warp in int32 (none, seven pairs, or all)."""
+    kernel: the two subjects of each slot pair share a warp; the longest pairs run first on
+    32-lane wavefronts (passes of 160 or 256 rows: none, seven pairs, or all); the rest run on
+    32-lane wavefronts (half 0), on two 16-lane wavefronts of 144-row passes per warp (half 1:
+    two slot pairs per item, an odd count leaving one wavefront empty), or on 32-lane
+    wavefronts up to pair 300 and 16-lane ones after it."""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
     monkeypatch.setenv("SWGB_LONG_PAIRS", long_pairs)
+    if half == "300":
+        monkeypatch.setenv("SWGB_PAIR_HALF_FROM", half)
+    else:
+        monkeypatch.setenv("SWGB_PAIR_HALF", half)
     rng = np.random.default_rng(1000 + m)
     lens = np.concatenate([rng.integers(0, 500, size=200), [0, 1, 31, 32, 33, 1200], rng.integers(0, 9, size=7)])
     db = w.database_from_lengths(rng, lens)          # 213 sequences: the last group has fillers
@@ -157,15 +165,22 @@ def test_two_subject_wavefront_matches_oracle(sw, m, long_pairs, monkeypatch):
         st = sw.sw_get_stats(h)
     _check(got[None], _oracle([q], db, sm, 10, 2), f"m={m}")
     assert st["intra_packed"] == 2 and st["inter_cells"] == 0
+    if half == "1":
+        assert st["wave_lanes"] == 16
+    elif half == "0":
+        assert st["wave_lanes"] == 32
 
 
+@pytest.mark.parametrize("half", ["0", "1"])
 @pytest.mark.parametrize("long_pairs", ["0", "100000"])
 @pytest.mark.parametrize("goe,ge", [(0, 0), (2, 9), (12, 2), (16383, 1), (16383, 16383)])
-def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, long_pairs, monkeypatch):
+def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, long_pairs, half, monkeypatch):
     """Gap regimes (the first phase unrolls the F recurrence when Goe + rows x min(Ge, Goe)
-    fits int16, and keeps the row-by-row chain otherwise), asymmetric matrix, 7 letters."""
+    fits int16, and keeps the row-by-row chain otherwise), asymmetric matrix, 7 letters, both
+    bulk shapes."""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
     monkeypatch.setenv("SWGB_LONG_PAIRS", long_pairs)
+    monkeypatch.setenv("SWGB_PAIR_HALF", half)
     rng = np.random.default_rng(7 * goe + ge)
     A = 7
     sm = rng.integers(-5, 9, size=(A, A)).astype(np.int8)     # asymmetric
@@ -179,14 +194,16 @@ def test_two_subject_gap_regimes_and_alphabet(sw, goe, ge, long_pairs, monkeypat
     _check(got[None], _oracle([q], db, sm, goe, ge), f"gaps {goe}/{ge}")
 
 
+@pytest.mark.parametrize("half", ["0", "1"])
 @pytest.mark.parametrize("flag_cap", [0, 1])
-def test_two_subject_saturation_rescored(sw, flag_cap, monkeypatch):
+def test_two_subject_saturation_rescored(sw, flag_cap, half, monkeypatch):
     """Hits above the int16 range in the two-subject mode: a matrix whose W/W entry is 120 lets
     a 300-residue query (whose profile fits in shared memory) score 36,000 against a run of W;
     those lanes are flagged and rescored in int32, with and without overflow of the list.  (No
     first phase: the planted subjects are among the longest, which it would align in int32.)"""
     monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
     monkeypatch.setenv("SWGB_LONG_PAIRS", "0")
+    monkeypatch.setenv("SWGB_PAIR_HALF", half)
     wl = w.plain(seed=41, scale=0.03)
     sm = wl.matrix.copy()
     sm[w.CODE_W, w.CODE_W] = 120
