@@ -26,6 +26,11 @@ __device__ __forceinline__ unsigned pack2mq(int v) {
 }
 
 // One column of one strip for both lanes (S' pairs read straight from the paired profile).
+// Rows go in sub-blocks of four: first X (and X - Goe) of the four rows from the previous
+// column's state -- row r's diagonal is row r - 1's H - Goe of the previous column, still in
+// Hm[r - 1] (for the first row of a sub-block it was saved in d before the previous sub-block
+// overwrote it) -- then the F chain down the sub-block, which overwrites Hm and E in place: the
+// operations of a row-by-row update of Eqs. sw2-sw4, with the four X independent of F.
 template <int kT>
 __device__ __forceinline__ void column_mq(unsigned (&Hm)[kT], unsigned (&E)[kT], unsigned& f,
                                           unsigned d, const uint32_t* prow, const PackedMq& k,
@@ -35,23 +40,20 @@ __device__ __forceinline__ void column_mq(unsigned (&Hm)[kT], unsigned (&E)[kT],
 #pragma unroll
     for (int r4 = 0; r4 < kT; r4 += 4) {
         const uint4 sv = p4[r4 >> 2];
-        const unsigned s[4] = {sv.x, sv.y, sv.z, sv.w};
+        const unsigned x0 = __viaddmax_s16x2_relu(d, sv.x, E[r4]);
+        const unsigned x1 = __viaddmax_s16x2_relu(Hm[r4], sv.y, E[r4 + 1]);
+        const unsigned x2 = __viaddmax_s16x2_relu(Hm[r4 + 1], sv.z, E[r4 + 2]);
+        const unsigned x3 = __viaddmax_s16x2_relu(Hm[r4 + 2], sv.w, E[r4 + 3]);
+        const unsigned xm[4] = {__viaddmax_s16x2(x0, k.ngoe, k.floor), __viaddmax_s16x2(x1, k.ngoe, k.floor),
+                                __viaddmax_s16x2(x2, k.ngoe, k.floor), __viaddmax_s16x2(x3, k.ngoe, k.floor)};
+        best = __vimax3_s16x2(best, x0, x1);
+        best = __vimax3_s16x2(best, x2, x3);
+        d = Hm[r4 + 3];   // old H - Goe of the sub-block's last row: the next sub-block's diagonal
 #pragma unroll
-        for (int h = 0; h < 4; h += 2) {
-            const int r = r4 + h;
-            const unsigned x0 = __viaddmax_s16x2_relu(d, s[h], E[r]);
-            const unsigned xm0 = __viaddmax_s16x2(x0, k.ngoe, k.floor);
-            d = Hm[r];
-            Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm0);
-            E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);
-            F = __viaddmax_s16x2(F, k.ngep, xm0);
-            const unsigned x1 = __viaddmax_s16x2_relu(d, s[h + 1], E[r + 1]);
-            const unsigned xm1 = __viaddmax_s16x2(x1, k.ngoe, k.floor);
-            d = Hm[r + 1];
-            Hm[r + 1] = __viaddmax_s16x2(F, k.ngoe, xm1);
-            E[r + 1] = __viaddmax_s16x2(E[r + 1], k.nge, Hm[r + 1]);
-            F = __viaddmax_s16x2(F, k.ngep, xm1);
-            best = __vimax3_s16x2(best, x0, x1);
+        for (int i = 0; i < 4; ++i) {
+            Hm[r4 + i] = __viaddmax_s16x2(F, k.ngoe, xm[i]);
+            E[r4 + i] = __viaddmax_s16x2(E[r4 + i], k.nge, Hm[r4 + i]);
+            F = __viaddmax_s16x2(F, k.ngep, xm[i]);
         }
     }
     f = F;
