@@ -60,24 +60,31 @@ __device__ __forceinline__ void column(unsigned (&Hm)[kT], unsigned (&E)[kT], un
         const uint4 b = pb[r8 >> 3];
         const unsigned wa[4] = {a.x, a.y, a.z, a.w};
         const unsigned wb[4] = {b.x, b.y, b.z, b.w};
+        // rows in sub-blocks of four: the four X (diagonals from the previous column's Hm,
+        // the first saved in d) before the F chain, which then overwrites Hm and E in place
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int r = r8 + 2 * h;
-            const unsigned s0 = __byte_perm(wa[h], wb[h], 0x5410);   // row r:   (lane a, lane b)
-            const unsigned s1 = __byte_perm(wa[h], wb[h], 0x7632);   // row r+1
-            const unsigned x0 = __viaddmax_s16x2_relu(d, s0, E[r]);
-            const unsigned xm0 = __viaddmax_s16x2(x0, k.ngoe, k.floor);
-            d = Hm[r];
-            Hm[r] = __viaddmax_s16x2(F, k.ngoe, xm0);
-            E[r] = __viaddmax_s16x2(E[r], k.nge, Hm[r]);
-            F = __viaddmax_s16x2(F, k.ngep, xm0);
-            const unsigned x1 = __viaddmax_s16x2_relu(d, s1, E[r + 1]);
-            const unsigned xm1 = __viaddmax_s16x2(x1, k.ngoe, k.floor);
-            d = Hm[r + 1];
-            Hm[r + 1] = __viaddmax_s16x2(F, k.ngoe, xm1);
-            E[r + 1] = __viaddmax_s16x2(E[r + 1], k.nge, Hm[r + 1]);
-            F = __viaddmax_s16x2(F, k.ngep, xm1);
+        for (int h4 = 0; h4 < 4; h4 += 2) {
+            const int r = r8 + 2 * h4;
+            unsigned sc[4];
+            sc[0] = __byte_perm(wa[h4], wb[h4], 0x5410);           // row r:   (lane a, lane b)
+            sc[1] = __byte_perm(wa[h4], wb[h4], 0x7632);           // row r + 1
+            sc[2] = __byte_perm(wa[h4 + 1], wb[h4 + 1], 0x5410);
+            sc[3] = __byte_perm(wa[h4 + 1], wb[h4 + 1], 0x7632);
+            const unsigned x0 = __viaddmax_s16x2_relu(d, sc[0], E[r]);
+            const unsigned x1 = __viaddmax_s16x2_relu(Hm[r], sc[1], E[r + 1]);
+            const unsigned x2 = __viaddmax_s16x2_relu(Hm[r + 1], sc[2], E[r + 2]);
+            const unsigned x3 = __viaddmax_s16x2_relu(Hm[r + 2], sc[3], E[r + 3]);
+            const unsigned xm[4] = {__viaddmax_s16x2(x0, k.ngoe, k.floor), __viaddmax_s16x2(x1, k.ngoe, k.floor),
+                                    __viaddmax_s16x2(x2, k.ngoe, k.floor), __viaddmax_s16x2(x3, k.ngoe, k.floor)};
             best = __vimax3_s16x2(best, x0, x1);
+            best = __vimax3_s16x2(best, x2, x3);
+            d = Hm[r + 3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                Hm[r + i] = __viaddmax_s16x2(F, k.ngoe, xm[i]);
+                E[r + i] = __viaddmax_s16x2(E[r + i], k.nge, Hm[r + i]);
+                F = __viaddmax_s16x2(F, k.ngep, xm[i]);
+            }
         }
     }
     f = F;
