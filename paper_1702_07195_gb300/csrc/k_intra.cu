@@ -189,6 +189,9 @@ __global__ void __launch_bounds__(kIBlock) k_intra_i32(const IntraParams p) {
         }
         return;
     }
+    // Launched as a programmatic dependent, the kernel may start while the kernel before it
+    // still runs: wait here for its completion and memory (no effect after an ordinary launch).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // Saturated lanes: the list first.  (Usually empty: then no warp touches the work counter,
     // whose atomics from every warp of the grid would otherwise serialise for microseconds.)
     const unsigned count = *reinterpret_cast<volatile unsigned*>(&p.ctrl->flag_count);
@@ -260,6 +263,24 @@ cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t
     if (e != cudaSuccess) return e;
     k_intra_i32<<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_intra_dependent(const IntraParams& p, int grid, int block, cudaStream_t st) {
+    const size_t smem = intra_smem_bytes(p.alphabet1);
+    cudaError_t e = cudaFuncSetAttribute(k_intra_i32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(block));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_intra_i32, p);
 }
 
 }  // namespace swgb

@@ -431,6 +431,9 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
     k.ngep = pack2(-p.gaps.gep);
     k.floor = 0x80008000u;
     const unsigned init_hm = k.ngoe, init_f = k.ngep;
+    // a rescore launched as a programmatic dependent may be scheduled now; it waits for this
+    // kernel's completion before it reads anything
+    asm volatile("griddepcontrol.launch_dependents;");
     const QueryDesc qd = p.queries[p.query];
     const int passes_l = max(1, (qd.m + kWarp * kTBL - 1) / (kWarp * kTBL));
     const int passes_b = kHalf ? max(1, (qd.m + kSsBulkLanes * kSsBulkRows - 1) / (kSsBulkLanes * kSsBulkRows)) : 0;
@@ -490,6 +493,16 @@ __global__ void __launch_bounds__(kSsBW * kWarp, kSsBlocksPerSM) k_wave_ss_i16x2
     if constexpr (kHalf)
         build(std::integral_constant<int, kSsBulkRows>{}, std::integral_constant<int, kSsBulkLanes>{},
               prof_b, passes_b);
+    // The int16 profile of the int32 rescore (query-major: qp_out[d * qp_mpad + i]), spread
+    // over the grid, when no separate kernel builds it.
+    if (p.qp_out) {
+        const int total = p.alphabet1 * p.qp_mpad;
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < total; v += gridDim.x * blockDim.x) {
+            const int d = v / p.qp_mpad, i = v - d * p.qp_mpad;
+            const int c = (d < A && i < qd.m) ? qres[i] : -1;
+            p.qp_out[v] = static_cast<int16_t>((c >= 0 && c < A ? s_mat[c * A + d] : 0) + p.qp_bias);
+        }
+    }
     __syncthreads();
 
     // Slot pair pi (0 = the longest): its group, pair index t, subject ids and lengths; an

@@ -694,6 +694,9 @@ sw_status build_plan(sw_db* db, const int64_t* h_qoff, int32_t nq, const int8_t*
         wp.spill = db->spill.ptr;
         wp.spill_stride = spill_stride;
         wp.gaps = gaps;
+        wp.qp_out = P.qp.ptr + qp_off[static_cast<size_t>(wp.query)];
+        wp.qp_mpad = mpad[static_cast<size_t>(wp.query)];
+        wp.qp_bias = P.qp_bias;
     }
     IntraParams& jp = P.intra;
     jp.plain = db->plain_ptr;
@@ -744,6 +747,12 @@ cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
                : cudaEventRecord(ev, st);
 }
 
+// A one-query search whose every group runs on the two-subject wavefront kernel.
+bool pair_only_plan(const sw_db* db, const Plan& P) {
+    return P.pair && P.int16_ok && P.num_items == 0 && !P.mq && db->layout.long_ids.empty() &&
+           P.g_pair_end == db->layout.num_groups && !P.wave;
+}
+
 // Enqueues the launch sequence of a plan on `st` (captured into a graph or run directly).
 sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_t st) {
     const int64_t N = db->layout.num_seqs;
@@ -753,22 +762,16 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
     for (int q = 0; q < P.nq; ++q)   // empty queries score 0 everywhere
         if (P.m[static_cast<size_t>(q)] == 0 && N > 0)
             CU(cudaMemsetAsync(P.d_scores + static_cast<int64_t>(q) * N, 0, sizeof(int32_t) * N, st));
-    // A one-query search that runs only the two-subject wavefront kernel (it builds its own
-    // profile) needs the int16 query profile for the rescore alone: build it on a side branch
-    // that joins before the rescore, off the critical path.
-    const bool qp_side = P.pair && P.num_items == 0 && db->layout.long_ids.empty() &&
-                         P.g_pair_end == db->layout.num_groups && !P.wave;
-    if (qp_side) {
-        CU(cudaEventRecord(db->fork_ev, st));
-        CU(cudaStreamWaitEvent(db->side_stream, db->fork_ev, 0));
-        CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
-                           P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, db->side_stream));
-        CU(cudaEventRecord(db->join_ev, db->side_stream));
-    } else {
+    // A one-query search that runs only the two-subject wavefront kernel (which builds its own
+    // profile) needs the int16 query profile for the rescore alone: that kernel writes it too,
+    // and the rescore follows as its programmatic dependent (launched while it runs, waiting
+    // for its completion), with no event node between them.
+    const bool pair_only = pair_only_plan(db, P);
+    if (!pair_only) {
         CU(launch_build_qp(d_queries, P.qoff.ptr, P.nq, P.matrix.ptr, db->A, P.qp_bias, P.qp_off.ptr,
                            P.mpad.ptr, P.qp.ptr, P.max_mpad, db->ctrl.ptr, st));
+        ++launches;
     }
-    ++launches;
     if (P.wave) {
         CU(launch_build_pp_wave(d_queries, P.qoff.ptr, P.wpasses.ptr, P.num_wpasses, P.wave_rows,
                                 P.matrix.ptr, db->A, P.qp_bias, P.wpp.ptr, P.wrows_pad,
@@ -816,6 +819,7 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
         if (P.pair) {
             WaveParams pp = P.pair_p;
             pp.qres = d_queries;
+            if (!pair_only) pp.qp_out = nullptr;
             CU(launch_wave_ss(pp, P.pair_rows, P.pair_half, static_cast<int>(max_m_of(P)), P.pair_grid, st));
             ++launches;
         }
@@ -826,13 +830,13 @@ sw_status enqueue_plan(sw_db* db, Plan& P, const uint8_t* d_queries, cudaStream_
             ++launches;
         }
     }
-    CU(record(db->ev[3], st));
-    if (qp_side) CU(cudaStreamWaitEvent(st, db->join_ev, 0));
+    if (!pair_only) CU(record(db->ev[3], st));
     if (P.int16_ok && (P.num_items > 0 || P.mq || P.wave || P.pair)) {
         // one block per SM: saturated lanes are rare (the list is usually empty, and a launch
         // of blocks that find it empty costs in proportion to their number)
         jp.mode = kIntraRescore;
-        CU(launch_intra(jp, std::min(P.intra_grid, db->sms), intra_block_threads(), st));
+        CU(pair_only ? launch_intra_dependent(jp, std::min(P.intra_grid, db->sms), intra_block_threads(), st)
+                     : launch_intra(jp, std::min(P.intra_grid, db->sms), intra_block_threads(), st));
         ++launches;
     }
     CU(record(db->ev[4], st));
@@ -949,6 +953,7 @@ sw_status search_device(sw_db* db, const uint8_t* d_queries, const int64_t* h_qo
     db->stats.graph_replay = replay ? 1 : 0;
     db->stats.variant = plan->variant;
     db->stats_inter = plan->mq || plan->num_items > 0;
+    db->stats_pair_only = pair_only_plan(db, *plan);
     db->stats_pending = true;
     return SW_OK;
 }
@@ -957,13 +962,18 @@ sw_status finish_stats(sw_db* db) {
     if (!db->stats_pending) return SW_OK;
     CU(cudaEventSynchronize(db->ev[4]));
     float t = 0;
-    t = 0;
     if (db->stats_inter) CU(cudaEventElapsedTime(&t, db->ev[1], db->ev[2]));
     db->stats.inter_ms = t;
-    CU(cudaEventElapsedTime(&t, db->ev[2], db->ev[3]));
-    db->stats.intra_ms = t;
-    CU(cudaEventElapsedTime(&t, db->ev[3], db->ev[4]));
-    db->stats.rescore_ms = t;
+    if (db->stats_pair_only) {   // no event between the wavefront kernel and its dependent rescore
+        CU(cudaEventElapsedTime(&t, db->ev[2], db->ev[4]));
+        db->stats.intra_ms = t;
+        db->stats.rescore_ms = 0;
+    } else {
+        CU(cudaEventElapsedTime(&t, db->ev[2], db->ev[3]));
+        db->stats.intra_ms = t;
+        CU(cudaEventElapsedTime(&t, db->ev[3], db->ev[4]));
+        db->stats.rescore_ms = t;
+    }
     CU(cudaEventElapsedTime(&t, db->ev[0], db->ev[4]));
     db->stats.total_ms = t;
     Control c{};
@@ -1098,9 +1108,6 @@ sw_status sw_db_load_ex(const uint8_t* residues, const int64_t* offsets, int64_t
     }
     CU(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&db->capture_stream, cudaStreamNonBlocking));
-    CU(cudaStreamCreateWithFlags(&db->side_stream, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&db->fork_ev, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&db->join_ev, cudaEventDisableTiming));
     for (auto& e : db->ev) CU(cudaEventCreate(&e));
     const Layout& L = db->layout;
     const size_t inter_bytes = static_cast<size_t>(std::max<int64_t>(L.inter_bytes, 16));
@@ -1184,9 +1191,6 @@ void sw_db_free(sw_db* db) {
             if (e) cudaEventDestroy(e);
         if (db->stream) cudaStreamDestroy(db->stream);
         if (db->capture_stream) cudaStreamDestroy(db->capture_stream);
-        if (db->side_stream) cudaStreamDestroy(db->side_stream);
-        if (db->fork_ev) cudaEventDestroy(db->fork_ev);
-        if (db->join_ev) cudaEventDestroy(db->join_ev);
     }
     delete db;
 }

@@ -145,8 +145,6 @@ struct sw_db {
     size_t pinned_q_cap = 0;
     cudaStream_t stream = nullptr;           // stream of the host-buffer API
     cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
-    cudaStream_t side_stream = nullptr;      // a parallel branch of a search (joined by events)
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaEvent_t ev[5] = {};                  // per-kernel timing; ev[4] = end of the last search
     bool done_recorded = false;
     std::vector<std::unique_ptr<swgb::Plan>> plans;   // most recent last, at most 32
@@ -164,6 +162,7 @@ struct sw_db {
     sw_stats stats{};
     bool stats_pending = false;
     bool stats_inter = false;    // the last search recorded the inter-task stage events
+    bool stats_pair_only = false;  // ... and ran the two-subject kernel with a dependent rescore
     std::mutex mu;
     ~sw_db() {
         if (host_inter) cudaFreeHost(host_inter);

@@ -8,7 +8,8 @@
 // no longer moves the bank) and lane l's chunk of kTB words sits at a lane-dependent offset
 // chosen so that the 8 lanes of every quarter-warp start in 8 different 16-byte bank groups.
 // With an odd number of rows per lane the chunks are packed (lane l at word kTB * l) and read
-// with 4-byte loads: kTB * l mod 32 is then a permutation of the banks.
+// with 4-byte loads: kTB * l mod 32 is then a permutation of the banks.  Two-word chunks (also
+// read with 4-byte loads) put lanes 16..31 one word further, on the odd banks.
 #pragma once
 
 #include "swgb_device.cuh"
@@ -24,7 +25,9 @@ namespace swgb {
 // 16 (the segment layout below).
 template <int kTB>
 __host__ __device__ constexpr int chunk_offset(int lane) {
-    if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1)) {
+    if constexpr (kTB == 2) {   // 4-byte loads: lanes 16..31 one word further, onto the odd banks
+        return 2 * lane + (lane >> 4);
+    } else if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1)) {
         return kTB * lane;
     } else {
         constexpr int w = kTB / 4;
@@ -38,7 +41,9 @@ __host__ __device__ constexpr int chunk_offset(int lane) {
 // Words per residue row of the slice: the span of the chunks rounded up to 32 words.
 template <int kTB>
 __host__ __device__ constexpr int slice_stride() {
-    if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1))
+    if constexpr (kTB == 2)
+        return (2 * kWarp + 1 + 31) / 32 * 32;
+    else if constexpr (kTB % 2 == 1 || (kTB % 4 == 0 && (kTB / 4) % 2 == 1))
         return (kTB * kWarp + 31) / 32 * 32;
     else
         return (4 * (33 * (kTB / 4) - 1) + 31) / 32 * 32;
@@ -47,7 +52,7 @@ __host__ __device__ constexpr int slice_stride() {
 template <int kTB>
 constexpr bool chunks_conflict_free() {
     bool ok = slice_stride<kTB>() % 32 == 0;   // the residue does not move the bank
-    if (kTB % 2 == 1) {
+    if (kTB % 2 == 1 || kTB == 2) {
         for (int k = 0; k < kTB; ++k) {        // 4-byte loads: one bank per lane
             unsigned long long seen = 0;
             for (int l = 0; l < kWarp; ++l) seen |= 1ull << ((chunk_offset<kTB>(l) + k) % 32);
@@ -72,7 +77,8 @@ constexpr bool chunks_conflict_free() {
         }
     return ok;
 }
-static_assert(chunks_conflict_free<3>() && chunks_conflict_free<4>() && chunks_conflict_free<5>() &&
+static_assert(chunks_conflict_free<1>() && chunks_conflict_free<2>() && chunks_conflict_free<3>() &&
+                  chunks_conflict_free<4>() && chunks_conflict_free<5>() &&
                   chunks_conflict_free<8>() && chunks_conflict_free<12>() && chunks_conflict_free<16>(),
               "profile slice layout");
 

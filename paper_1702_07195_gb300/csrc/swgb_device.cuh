@@ -214,6 +214,9 @@ struct WaveParams {
     int32_t prefix_f;           // first phase: F recurrence unrolled (Goe + rows x Ge' < 2^15)
     int64_t half_from;          // two-subject mode: pairs from here on run two per warp item
                                 //   on 16-lane wavefronts (kernels built for it)
+    int16_t* qp_out;            // two-subject mode, non-null: also write the query's int16
+    int32_t qp_mpad;            //   profile (qp_out[d * qp_mpad + i] = SM + qp_bias) for the
+    int32_t qp_bias;            //   int32 rescore that follows as a dependent launch
     int32_t alphabet1;
     Control* ctrl;
     FlagEntry* flags;
@@ -286,6 +289,10 @@ cudaError_t launch_build_pp(const uint8_t* d_queries, const int64_t* d_qoff, con
                             int32_t bias, uint32_t* d_pp, int64_t rows_pad, Control* ctrl,
                             cudaStream_t st);
 cudaError_t launch_intra(const IntraParams& p, int grid, int block, cudaStream_t st);
+// The same launch as a programmatic dependent of the kernel launched just before it on `st`: its
+// blocks may become resident while that kernel runs and wait (griddepcontrol.wait) for its
+// completion and memory before reading anything it wrote.
+cudaError_t launch_intra_dependent(const IntraParams& p, int grid, int block, cudaStream_t st);
 // Block-shared-profile variant for the kIntraLong and kIntraGroups work sources (4 warps,
 // 8 or 16 query rows per lane).
 // Query rows per lane of the block int32 kernel's variants (passes of 160, 256 and 512 rows).
