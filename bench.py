@@ -222,7 +222,9 @@ def measured_peaks():
 
 KERNEL_SRC = {"k_inter_i16x2": os.path.join(CSRC, "k_inter.cu"),
               "k_inter_mq_i16x2": os.path.join(CSRC, "k_inter_mq.cu"),
-              "k_intra_block_i32": os.path.join(CSRC, "k_intra_block.cu")}
+              "k_intra_block_i32": os.path.join(CSRC, "k_intra_block.cu"),
+              "k_wave_mq_i16x2": os.path.join(CSRC, "k_wave.cu"),
+              "k_wave_ss_i16x2": os.path.join(CSRC, "k_wave.cu")}
 
 # rows per strip of the inter-task kernel variants (both kernels), as in csrc/k_inter*.cu
 INTER_VARIANT_ROWS = (32, 64, 32, 64)
