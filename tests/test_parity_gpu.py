@@ -291,6 +291,30 @@ def test_multi_query_kernel_matches_oracle(sw, variant, monkeypatch):
     _check(got2, exp, "single-query kernel")
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_multi_query_many_short_queries(sw, variant, seed, monkeypatch):
+    """A batch of twenty-one queries, most shorter than one strip (lengths around 16-row
+    multiples, two of length 1, one empty) plus a saturating query (int32 rescore): many
+    query boundaries in both streams of the multi-query kernel, for every variant; every score
+    equals the oracle."""
+    monkeypatch.setenv("SWGB_GROUP_SPLIT", "1000000000")   # keep every group on the int16 path
+    rng = np.random.default_rng(300 + 10 * variant + seed)
+    base = w.batched(seed=15 + seed, scale=0.002).db
+    db2, q_sat, _ = w.plant_saturating(base, w.draw_residues(rng, 20), count=2, run=3100)
+    lens = [16, 17, 48, 5, 33, 64, 80, 15, 1, 1, 100, 47, 31, 16, 0, 200, 3, 9, 112, 129]
+    rng.shuffle(lens)
+    qs = [w.draw_residues(rng, n) for n in lens] + [q_sat]
+    sm = w.blosum62()
+    exp = _oracle_all(qs, db2, sm, 10, 2)
+    with sw.sw_db_load(db2.residues, db2.offsets, w.ALPHABET_SIZE, long_cutoff=4096) as h:
+        sw.sw_db_set_variant(h, variant)
+        got = sw.sw_search_batch(h, qs, sm, 10, 2)
+        st = sw.sw_get_stats(h)
+        assert st["multi_query"] == 1 and st["flagged"] >= 2
+    _check(got, exp, f"short queries, variant {variant}")
+
+
 @pytest.mark.parametrize("split", ["0", "1", "3", "auto"])
 def test_group_routing_to_intra_kernel(sw, split, monkeypatch):
     """Groups above the split run on the int32 intra-task kernel (one warp per pair); the
