@@ -217,6 +217,30 @@ def test_two_subject_saturation_rescored(sw, flag_cap, half, monkeypatch):
     assert exp.max() > 32767 and st["flagged"] >= 3 and st["intra_packed"] == 2
 
 
+@pytest.mark.parametrize("long_pairs", ["0", "500"])
+@pytest.mark.parametrize("m", [1, 33, 144, 160, 250])
+def test_two_subject_many_pairs_per_warp(sw, m, long_pairs, monkeypatch):
+    """A one-pass query (160 rows, or 256 for m = 250) against 24,000 subjects: about ten slot
+    pairs per warp from the work queue, with and without a first phase.  Lengths mix empty
+    subjects, very short ones, the bulk of the length law and a few long ones."""
+    monkeypatch.setenv("SWGB_GROUP_SPLIT", "0")
+    monkeypatch.setenv("SWGB_LONG_PAIRS", long_pairs)
+    monkeypatch.setenv("SWGB_PAIR_HALF", "0")
+    rng = np.random.default_rng(77 + m)
+    n = 24000
+    lens = np.where(rng.random(n) < 0.3, rng.integers(0, 40, size=n),
+                    np.clip(rng.lognormal(4.3, 0.6, size=n), 1, 1500).astype(np.int64))
+    lens[rng.integers(0, n, size=40)] = rng.integers(600, 1500, size=40)
+    db = w.database_from_lengths(rng, lens)
+    q = w.draw_residues(rng, m)
+    sm = w.blosum62()
+    with sw.sw_db_load(db.residues, db.offsets, w.ALPHABET_SIZE) as h:
+        got = sw.sw_search(h, q, sm, 10, 2)
+        st = sw.sw_get_stats(h)
+    _check(got[None], _oracle([q], db, sm, 10, 2), f"many pairs per warp, m={m}")
+    assert st["intra_packed"] == 2 and st["inter_cells"] == 0 and st["wave_lanes"] == 32
+
+
 def test_two_subject_equals_int32_kernel(sw, monkeypatch):
     wl = w.plain(seed=3, scale=0.3)
     with sw.sw_db_load(wl.db.residues, wl.db.offsets, w.ALPHABET_SIZE) as h:
