@@ -212,11 +212,6 @@ struct WaveParams {
     int64_t long_pairs;         // two-subject mode: the longest slot pairs, served first ...
     int32_t long_blocks;        // ... by a few warps of blocks [0, long_blocks)
     int32_t prefix_f;           // first phase: F recurrence unrolled (Goe + rows x Ge' < 2^15)
-    int64_t half_from;          // two-subject mode: pairs from here on run two per warp item
-                                //   on 16-lane wavefronts (kernels built for it)
-    int16_t* qp_out;            // two-subject mode, non-null: also write the query's int16
-    int32_t qp_mpad;            //   profile (qp_out[d * qp_mpad + i] = SM + qp_bias) for the
-    int32_t qp_bias;            //   int32 rescore that follows as a dependent launch
     int32_t alphabet1;
     Control* ctrl;
     FlagEntry* flags;
@@ -225,6 +220,13 @@ struct WaveParams {
     int2* spill;                // per resident warp: pass-boundary row, one int2 per column
     int64_t spill_stride;
     Gaps gaps;
+    // (the two-subject fields below come last: placed before alphabet1, which shifts the
+    // fields the two-query kernel reads, they cost that kernel 1.6 % on the long-subject mix)
+    int64_t half_from;          // two-subject mode: pairs from here on run two per warp item
+                                //   on 16-lane wavefronts (kernels built for it)
+    int16_t* qp_out;            // two-subject mode, non-null: also write the query's int16
+    int32_t qp_mpad;            //   profile (qp_out[d * qp_mpad + i] = SM + qp_bias) for the
+    int32_t qp_bias;            //   int32 rescore that follows as a dependent launch
 };
 constexpr int kWaveRows[3] = {8, 12, 16};   // query rows per lane of the two-query variants
 int wave_warps();
