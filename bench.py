@@ -413,16 +413,18 @@ def e2e_measure(sw, db, wl, steps, barrier=lambda: None, reduce_max=lambda x: x)
         *[ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_uint8)) for t in h_q])
     lens = np.array([len(q) for q in wl.queries], np.int32)
     mat = np.ascontiguousarray(wl.matrix, np.int8)
+    # the call's arguments are marshalled once, outside the timed loop: each step is the C-ABI
+    # call (queries copied in, every score copied out) and a host read of its result
+    fn, handle, gap_open, gap_extend = sw.lib.sw_search_batch, db.handle, wl.gap_open, wl.gap_extend
+    p_lens = lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p_mat = mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+    p_s = ctypes.cast(h_s.data_ptr(), ctypes.POINTER(ctypes.c_int32))
+    h_view = h_s.numpy()
 
     def e2e_step():
-        s = sw.lib.sw_search_batch(db.handle, arr,
-                                   lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nq,
-                                   mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
-                                   wl.gap_open, wl.gap_extend,
-                                   ctypes.cast(h_s.data_ptr(), ctypes.POINTER(ctypes.c_int32)))
-        if s != 0:
+        if fn(handle, arr, p_lens, nq, p_mat, gap_open, gap_extend, p_s) != 0:
             raise RuntimeError(sw.sw_last_error())
-        return int(h_s[0])   # read of the step's result on the host
+        return int(h_view[0])   # read of the step's result on the host
 
     e2e_step()
     barrier()
@@ -480,13 +482,45 @@ def check_oracle_sample(wl, got, count, seed):
 
 def check_oracle_all(wl, got):
     import oracle
-    bad = 0
+    bad, cores, oracle_s = 0, 0, 0.0
     for q in range(len(wl.queries)):
-        exp, _ = oracle.sw_search(wl.queries[q], wl.db.residues, wl.db.offsets, wl.matrix,
-                                  wl.gap_open, wl.gap_extend)
+        t0 = time.perf_counter()
+        exp, cores = oracle.sw_search(wl.queries[q], wl.db.residues, wl.db.offsets, wl.matrix,
+                                      wl.gap_open, wl.gap_extend)
+        oracle_s += time.perf_counter() - t0
         bad += int(np.count_nonzero(got[q].astype(np.int64) != exp))
     return {"ok": bad == 0, "scores_checked": int(got.size),
-            "how": "every score recomputed by the oracle", "mismatches": bad}
+            "how": "every score recomputed by the oracle", "mismatches": bad,
+            "oracle_s": round(oracle_s, 3), "oracle_cores": int(cores)}
+
+
+# fixed seeded samples of database sequences for the oracle timing of the larger configurations
+# (10-20 s of CPU work each on 16 cores): 0.1 % of the paper-shaped database, 16 of the
+# long-subject database's 50,000 subjects (each 5,000-35,000 residues)
+CONFIG_CPU_SAMPLE = {"paper_shaped": lambda n: max(16, int(round(n * 0.001))),
+                     "long_subject": lambda n: min(n, 16)}
+
+
+def config_cpu_baseline(name, wl, par):
+    """The oracle timed on a configuration: the whole plain configuration (its parity check runs
+    the oracle over every score), a fixed seeded sample of the larger databases."""
+    cells_q = sum(len(q) for q in wl.queries)
+    if name == "plain" and "oracle_s" in par:
+        return {"value": cells_q * wl.db.num_residues / par["oracle_s"] / 1e9, "unit": "GCUPS",
+                "cores": par["oracle_cores"], "kind": "oracle",
+                "sample": f"the whole configuration ({wl.db.num_seqs} sequences, "
+                          f"{cells_q * wl.db.num_residues:.3e} cells), timed in {par['oracle_s']:.2f} s"}
+    if name not in CONFIG_CPU_SAMPLE:
+        return None
+    n = wl.db.num_seqs
+    idx = w.sample_indices(n, CONFIG_CPU_SAMPLE[name](n), seed=CPU_SAMPLE_SEED)
+    sub = wl.db.subset(idx)
+    dt, cores = time_oracle(wl, sub)
+    cells = cells_q * sub.num_residues
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"all {len(wl.queries)} queries vs a fixed seeded sample of the database "
+                      f"(seed {CPU_SAMPLE_SEED}: {len(idx)} of {n} sequences, {cells:.3e} cells), "
+                      f"timed in {dt:.1f} s"}
 
 
 def parity(name, wl, got):
@@ -650,6 +684,10 @@ def measure_extra(sw, name, args, sampler, sms, f_max, peaks, peak_src):
             if not np.array_equal(h_got, got):
                 out["e2e"]["mismatch_vs_device_path"] = True
         out["parity"] = parity(name, wl, got)
+        if not args.no_cpu_baseline:
+            cb = config_cpu_baseline(name, wl, out["parity"])
+            if cb is not None:
+                out["cpu_baseline"] = cb
         torch.cuda.synchronize()
         return out
     finally:
