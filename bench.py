@@ -533,6 +533,7 @@ def parity(name, wl, got):
     extra = check_oracle_sample(wl, got, 64, seed=5)
     out["ok"] = out["ok"] and extra["ok"]
     out["scores_checked"] += extra["scores_checked"]
+    out["mismatches"] = (out.get("mismatches", []) + extra["mismatches"])[:5]
     out["how"] = (out.get("how", "") + "; " if doc is not None else "") + extra["how"]
     return out
 
