@@ -109,7 +109,7 @@ WORKLOAD_TEXT = {
 }
 
 # Steps of the workloads measured after the headline: (warm-up, timed, end-to-end timed).
-EXTRA_STEPS = {"plain": (5, 50, 20), "long_subject": (3, 3, 2), "paper_shaped": (3, 2, 1)}
+EXTRA_STEPS = {"plain": (10, 400, 50), "long_subject": (3, 3, 2), "paper_shaped": (3, 2, 1)}
 
 
 def make_workload(name, seed, scale, query_lengths=""):
