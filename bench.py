@@ -286,15 +286,24 @@ def cpu_sample(wl):
     return idx, wl.db.subset(idx)
 
 
+def host_cores() -> int:
+    """Host cores this process may run on (a launcher such as torchrun sets OMP_NUM_THREADS=1
+    for its workers, so the oracle is given the count explicitly)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def time_oracle(wl, sub):
     """Times the oracle (as it stands, all host cores) on every query against `sub`."""
     import oracle
     oracle.build()
-    cores = 0
+    cores, threads = 0, host_cores()
     t0 = time.perf_counter()
     for q in wl.queries:
         _, cores = oracle.sw_search(q, sub.residues, sub.offsets, wl.matrix, wl.gap_open,
-                                    wl.gap_extend)
+                                    wl.gap_extend, threads=threads)
     return time.perf_counter() - t0, int(cores)
 
 
