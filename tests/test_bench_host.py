@@ -65,3 +65,15 @@ def test_stored_headline_results_match_the_generated_inputs():
     wl = bench.make_workload("batched", 0, 1.0)
     doc = bench.load_golden("batched", wl)
     assert doc is not None and len(doc["rows"]) == len(wl.queries) == 20
+
+
+@pytest.mark.parametrize("kernel,workload", [("k_inter_mq_i16x2", "batched"),
+                                             ("k_inter_mq_i16x2", "paper_shaped"),
+                                             ("k_wave_mq_i16x2", "long_subject"),
+                                             ("k_wave_ss_i16x2", "plain")])
+def test_profiles_of_the_reported_kernels_are_current(kernel, workload):
+    """The ncu summary the bench reads for each configuration's dominant kernel was taken on
+    the kernel source as it is now (else the bench reports its traffic as unknown)."""
+    rows = {"batched": 64, "paper_shaped": 32}.get(workload)
+    traffic = bench.ncu_traffic(workload, kernel, rows_per_strip=rows)
+    assert traffic is not None and traffic > 0
