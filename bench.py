@@ -491,11 +491,11 @@ def check_oracle_sample(wl, got, count, seed):
 
 def check_oracle_all(wl, got):
     import oracle
-    bad, cores, oracle_s = 0, 0, 0.0
+    bad, cores, oracle_s, threads = 0, 0, 0.0, host_cores()
     for q in range(len(wl.queries)):
         t0 = time.perf_counter()
         exp, cores = oracle.sw_search(wl.queries[q], wl.db.residues, wl.db.offsets, wl.matrix,
-                                      wl.gap_open, wl.gap_extend)
+                                      wl.gap_open, wl.gap_extend, threads=threads)
         oracle_s += time.perf_counter() - t0
         bad += int(np.count_nonzero(got[q].astype(np.int64) != exp))
     return {"ok": bad == 0, "scores_checked": int(got.size),
@@ -504,7 +504,7 @@ def check_oracle_all(wl, got):
 
 
 # fixed seeded samples of database sequences for the oracle timing of the larger configurations
-# (10-20 s of CPU work each on 16 cores): 0.1 % of the paper-shaped database, 16 of the
+# (15-25 s of CPU work each on 16 cores): 0.1 % of the paper-shaped database, 16 of the
 # long-subject database's 50,000 subjects (each 5,000-35,000 residues)
 CONFIG_CPU_SAMPLE = {"paper_shaped": lambda n: max(16, int(round(n * 0.001))),
                      "long_subject": lambda n: min(n, 16)}
